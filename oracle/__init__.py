@@ -1,0 +1,283 @@
+"""FP64 CPU oracle for preconditioned data sparsification.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  The product
+path (``paper_1511_00152_gb300``) never imports it, and this package never
+imports the product.
+
+The arithmetic lives in ``sk_oracle.c`` (plain single-threaded C loops in
+double precision); this module compiles it with gcc on first use and wraps
+each routine with numpy arrays.  The one library routine used is LAPACK's
+symmetric eigensolver (``numpy.linalg.eigh``) for the PCA step.
+
+Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
+  philox4x32_10   -- known-answer vectors published with Random123 (SC'11)
+  signs, mask     -- distribution tests: P(keep j) = m/p (Lemma B2), ordered
+                     m-tuples uniform, exactly m distinct indices, m = p gives
+                     a permutation; Lemire rejection driven by explicit words
+  fwht            -- explicit Sylvester matrix at p <= 64, orthonormality,
+                     involution, norm preservation (Sec. III)
+  compress        -- the above plus the gather identity val = y[idx]
+  gram/cov        -- exhaustive enumeration of every mask at p = 8: the mask
+                     average equals C_emp (unbiasedness, Sec. V / Appendix C);
+                     m = p reduces to (1/n) Y^T Y exactly
+  sample_mean     -- exhaustive enumeration: unbiased (Sec. IV)
+  kmeans          -- m = p reduces to Lloyd's on H D X (Sec. VI-A), brute-force
+                     argmin on tiny inputs, J' non-increasing (Sec. VI-B)
+  unmix           -- D H (H D x) = x; back-map (HD)^T C_emp(Y) (HD) = C_emp(X)
+  pca_topk        -- LAPACK eigh (library); compared as subspaces
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sk_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libsk_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TAG_SIGN = 0x5349474E
+TAG_MASK = 0x4D41534B
+TAG_INIT = 0x494E4954
+
+
+def build(force: bool = False) -> str:
+    """Compile sk_oracle.c into a shared library (gcc, -O2, no vector ISA flags)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, u64, u32, vp = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+        sig = {
+            "oracle_philox4x32_10": (None, [vp, vp, vp]),
+            "oracle_ptilde": (i64, [i64]),
+            "oracle_lemire_from_words": (u32, [u32, vp, i64, vp]),
+            "oracle_signs": (None, [i64, u64, vp]),
+            "oracle_mask": (None, [i64, i64, u64, i64, vp]),
+            "oracle_init_rows": (None, [i64, i64, u64, vp]),
+            "oracle_fwht": (None, [vp, i64]),
+            "oracle_precondition": (None, [vp, i64, i64, i64, u64, vp]),
+            "oracle_compress": (None, [vp, i64, i64, i64, i64, i64, u64, vp, vp]),
+            "oracle_gram": (None, [vp, vp, i64, i64, i64, vp]),
+            "oracle_cov_finalize": (None, [vp, i64, i64, i64, vp]),
+            "oracle_sample_mean": (None, [vp, vp, i64, i64, i64, vp]),
+            "oracle_kmeans_assign": (None, [vp, vp, i64, i64, vp, i64, i64, vp, vp]),
+            "oracle_kmeans_update": (None, [vp, vp, vp, i64, i64, i64, i64, vp, vp, vp, vp]),
+            "oracle_unmix": (None, [vp, i64, i64, i64, u64, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------- RNG spec
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: ctr is 4 uint32 words, key is 2 uint32 words."""
+    c = _c(ctr, np.uint32)
+    k = _c(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    _load().oracle_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def lemire_from_words(s: int, words) -> tuple[int, int]:
+    """U(s) drawn from an explicit word list: (value, words consumed or -1)."""
+    w = _c(words, np.uint32)
+    used = np.zeros(1, np.int64)
+    v = _load().oracle_lemire_from_words(int(s), _p(w), w.size, _p(used))
+    return int(v), int(used[0])
+
+
+def ptilde(p: int) -> int:
+    return int(_load().oracle_ptilde(int(p)))
+
+
+def signs(pt: int, seed: int) -> np.ndarray:
+    """Diagonal of D as +-1.0 (Sec. III)."""
+    D = np.zeros(pt, np.float64)
+    _load().oracle_signs(pt, seed, _p(D))
+    return D
+
+
+def mask(pt: int, m: int, seed: int, row: int) -> np.ndarray:
+    """Omega_r: m distinct indices of [0, pt) in draw order."""
+    out = np.zeros(max(m, 1), np.int32)
+    _load().oracle_mask(pt, m, seed, row, _p(out))
+    return out[:m]
+
+
+def init_rows(n: int, K: int, seed: int) -> np.ndarray:
+    """K distinct row indices of [0, n) (seeded K-means start for the harness)."""
+    out = np.zeros(max(K, 1), np.int64)
+    _load().oracle_init_rows(n, K, seed, _p(out))
+    return out[:K]
+
+
+# ------------------------------------------------------------ preconditioner
+
+def fwht(y) -> np.ndarray:
+    """Orthonormal Sylvester Walsh-Hadamard transform of a length-2^L vector."""
+    a = _c(y, np.float64).copy()
+    _load().oracle_fwht(_p(a), a.size)
+    return a
+
+
+def precondition(X, seed: int) -> np.ndarray:
+    """Y = H D [X, 0] row by row (n x pt), from float32 samples."""
+    X = _c(X, np.float32)
+    n, p = X.shape
+    pt = ptilde(p)
+    Y = np.zeros((n, pt), np.float64)
+    _load().oracle_precondition(_p(X), n, p, p, seed, _p(Y))
+    return Y
+
+
+def compress(X, m: int, seed: int, row0: int = 0):
+    """ELL form (idx int32 n x m, val float64 n x m) of rows row0.. of X."""
+    X = _c(X, np.float32)
+    n, p = X.shape
+    idx = np.zeros((n, m), np.int32)
+    val = np.zeros((n, m), np.float64)
+    _load().oracle_compress(_p(X), n, p, p, row0, m, seed, _p(idx), _p(val))
+    return idx, val
+
+
+# ---------------------------------------------------------------- estimators
+
+def gram(idx, val, pt: int, G=None) -> np.ndarray:
+    """G += sum_i w_i w_i^T (pt x pt)."""
+    idx = _c(idx, np.int32)
+    val = _c(val, np.float64)
+    n, m = idx.shape
+    if G is None:
+        G = np.zeros((pt, pt), np.float64)
+    assert G.flags.c_contiguous and G.dtype == np.float64
+    _load().oracle_gram(_p(idx), _p(val), n, m, pt, _p(G))
+    return G
+
+
+def cov_finalize(G, n: int, m: int) -> np.ndarray:
+    """C_n from the accumulated Gram of n rows (Sec. V)."""
+    G = _c(G, np.float64)
+    pt = G.shape[0]
+    C = np.zeros_like(G)
+    _load().oracle_cov_finalize(_p(G), n, m, pt, _p(C))
+    return C
+
+
+def cov(idx, val, pt: int) -> np.ndarray:
+    idx = np.asarray(idx)
+    return cov_finalize(gram(idx, val, pt), idx.shape[0], idx.shape[1])
+
+
+def sample_mean(idx, val, pt: int) -> np.ndarray:
+    idx = _c(idx, np.int32)
+    val = _c(val, np.float64)
+    n, m = idx.shape
+    out = np.zeros(pt, np.float64)
+    _load().oracle_sample_mean(_p(idx), _p(val), n, m, pt, _p(out))
+    return out
+
+
+def pca_topk(C, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Top-k eigenpairs of the symmetric estimate C (LAPACK eigh, FP64).
+
+    Returns (eigenvalues descending, eigenvectors as columns).  The sign of
+    each vector makes its largest-magnitude entry positive."""
+    w, V = np.linalg.eigh(np.asarray(C, np.float64))
+    order = np.argsort(w)[::-1][:k]
+    w, V = w[order], V[:, order].copy()
+    for c in range(V.shape[1]):
+        j = np.argmax(np.abs(V[:, c]))
+        if V[j, c] < 0:
+            V[:, c] = -V[:, c]
+    return w, V
+
+
+def kmeans_assign(idx, val, mu, pt: int):
+    idx = _c(idx, np.int32)
+    val = _c(val, np.float64)
+    mu = _c(mu, np.float64)
+    n, m = idx.shape
+    K = mu.shape[0]
+    labels = np.zeros(n, np.int32)
+    dist = np.zeros(n, np.float64)
+    _load().oracle_kmeans_assign(_p(idx), _p(val), n, m, _p(mu), K, pt, _p(labels), _p(dist))
+    return labels, dist
+
+
+def kmeans_update(idx, val, labels, mu_prev, pt: int):
+    idx = _c(idx, np.int32)
+    val = _c(val, np.float64)
+    labels = _c(labels, np.int32)
+    mu_prev = _c(mu_prev, np.float64)
+    n, m = idx.shape
+    K = mu_prev.shape[0]
+    mu_new = np.zeros_like(mu_prev)
+    counts = np.zeros((K, pt), np.int64)
+    nk = np.zeros(K, np.int64)
+    _load().oracle_kmeans_update(_p(idx), _p(val), _p(labels), n, m, K, pt, _p(mu_prev),
+                                 _p(mu_new), _p(counts), _p(nk))
+    return mu_new, counts, nk
+
+
+def kmeans_objective(idx, val, labels, mu) -> float:
+    """J'(c, mu') of Sec. VI-A: sum_i || z_i - R_i^T mu'_{c_i} ||^2."""
+    idx = np.asarray(idx)
+    val = np.asarray(val, np.float64)
+    mu = np.asarray(mu, np.float64)
+    diff = val - mu[np.asarray(labels)[:, None], idx]
+    return float(np.sum(diff * diff))
+
+
+def kmeans(idx, val, mu0, pt: int, iters: int):
+    """Sparsified K-means iterations (Algorithm 1, loop body): assign, then update."""
+    mu = np.array(mu0, np.float64, copy=True)
+    history = []
+    labels = None
+    for _ in range(iters):
+        labels, _d = kmeans_assign(idx, val, mu, pt)
+        history.append(kmeans_objective(idx, val, labels, mu))
+        mu, _counts, _nk = kmeans_update(idx, val, labels, mu, pt)
+    return labels, mu, history
+
+
+def unmix(M, p: int, seed: int) -> np.ndarray:
+    """mu = D H mu' truncated to p coordinates, row by row (Eq. (mu-mu'))."""
+    M = _c(M, np.float64)
+    r, pt = M.shape
+    out = np.zeros((r, p), np.float64)
+    _load().oracle_unmix(_p(M), r, pt, p, seed, _p(out))
+    return out

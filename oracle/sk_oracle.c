@@ -1,0 +1,307 @@
+/*
+ * sk_oracle.c -- plain, slow, FP64 CPU oracle for preconditioned data
+ * sparsification (Pourkamali-Anaraki & Becker, "Preconditioned Data
+ * Sparsification for Big Data with Applications to PCA and K-means").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this
+ * file; only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark do.  It shares no code with the CUDA library: the random
+ * number spec below is implemented here a second time, from its
+ * published definitions, so that agreement between the two sides is
+ * evidence rather than tautology.
+ *
+ * Every routine is a direct, single-threaded loop over the definition it
+ * cites.  Floating point is double throughout.  Input samples arrive as
+ * float (the data type the GPU path reads) and are widened on load.
+ *
+ * Written random-number spec (shared in prose with the CUDA side):
+ *   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11 "Parallel random
+ *   numbers: as easy as 1, 2, 3"), key = (seed_lo, seed_hi).
+ *   Signs D (Sec. III, Eq. (ROS)): coordinate j uses bit (j mod 32) of
+ *     output word (j/32) mod 4 of Philox(ctr = (j/128, 0, 0, TAG_SIGN));
+ *     bit 0 -> D_j = +1, bit 1 -> D_j = -1.  One D for the whole data set.
+ *   Mask of global row r (Sec. I-A, Thm. B1): words w = 0,1,2,... are
+ *     output word (w mod 4) of Philox(ctr = (w/4, r_lo, r_hi, TAG_MASK)).
+ *     Bounded integers in [0,s) by Lemire's multiply-shift with rejection
+ *     (D. Lemire, "Fast random integer generation in an interval", ACM
+ *     TOMACS 2019).  Partial Fisher-Yates over the virtual identity array
+ *     a[0..pt): for t = 0..m-1, k = t + U(pt - t), swap a[t], a[k],
+ *     emit a[t].  Indices are kept in draw order.
+ *   Initial K-means rows (test harness): partial Fisher-Yates over [0,n)
+ *     with words of Philox(ctr = (w/4, 0, 0, TAG_INIT)).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TAG_SIGN 0x5349474Eu /* "SIGN" */
+#define TAG_MASK 0x4D41534Bu /* "MASK" */
+#define TAG_INIT 0x494E4954u /* "INIT" */
+
+/* ---------------- Philox4x32-10 (Salmon et al., SC'11) ---------------- */
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u; /* round multipliers */
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u; /* Weyl key bumps */
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k[2] = {key_in[0], key_in[1]};
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k[0] += W0;
+            k[1] += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k[0];
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c[3] ^ k[1];
+        uint32_t n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Word w of the stream (c1, c2, tag) under key seed. */
+static uint32_t stream_word(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
+                            uint64_t w) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)(w / 4), c1, c2, tag};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[w % 4];
+}
+
+/* Smallest power of two >= p (the padded dimension p~). */
+int64_t oracle_ptilde(int64_t p) {
+    int64_t q = 1;
+    while (q < p) q *= 2;
+    return q;
+}
+
+/* ---------------- Lemire bounded integer ---------------- */
+
+/* U(s) from an explicit word list (exposed so tests can drive rejection).
+ * Returns the value; *consumed receives how many words were used, or -1
+ * if the list ran out. */
+uint32_t oracle_lemire_from_words(uint32_t s, const uint32_t *words, int64_t nwords,
+                                  int64_t *consumed) {
+    int64_t used = 0;
+    uint32_t threshold = (uint32_t)(((uint64_t)1 << 32) % s); /* 2^32 mod s */
+    for (;;) {
+        if (used >= nwords) { *consumed = -1; return 0; }
+        uint64_t L = (uint64_t)words[used++] * (uint64_t)s;
+        uint32_t low = (uint32_t)L;
+        if (low < threshold) continue; /* reject: keeps U(s) exactly uniform */
+        *consumed = used;
+        return (uint32_t)(L >> 32);
+    }
+}
+
+/* ---------------- Signs D (Sec. III, Eq. (ROS)) ---------------- */
+
+void oracle_signs(int64_t pt, uint64_t seed, double *D) {
+    for (int64_t j = 0; j < pt; ++j) {
+        uint32_t word = stream_word(seed, 0u, 0u, TAG_SIGN, (uint64_t)(j / 32));
+        /* stream_word(w) takes word w of block w/4: coordinate j lives in
+         * block j/128, word (j/32) mod 4 -> stream word index j/32. */
+        uint32_t bit = (word >> (j % 32)) & 1u;
+        D[j] = bit ? -1.0 : 1.0;
+    }
+}
+
+/* ---------------- Mask Omega_r (Sec. I-A; Thm. B1) ---------------- */
+
+/* Partial Fisher-Yates over a[0..pt) on the virtual identity array, stored
+ * here as an explicit array (this is the slow, obvious form). */
+static void fisher_yates_stream(int64_t N, int64_t m, uint64_t seed, uint32_t c1,
+                                uint32_t c2, uint32_t tag, int64_t *out) {
+    int64_t *a = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    for (int64_t j = 0; j < N; ++j) a[j] = j;
+    uint64_t w = 0;
+    for (int64_t t = 0; t < m; ++t) {
+        uint32_t s = (uint32_t)(N - t);
+        uint32_t threshold = (uint32_t)(((uint64_t)1 << 32) % s);
+        uint64_t L;
+        for (;;) {
+            uint32_t v = stream_word(seed, c1, c2, tag, w++);
+            L = (uint64_t)v * (uint64_t)s;
+            if ((uint32_t)L >= threshold) break;
+        }
+        int64_t k = t + (int64_t)(L >> 32);
+        int64_t tmp = a[t];
+        a[t] = a[k];
+        a[k] = tmp;
+        out[t] = a[t];
+    }
+    free(a);
+}
+
+void oracle_mask(int64_t pt, int64_t m, uint64_t seed, int64_t row, int32_t *omega) {
+    int64_t *tmp = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    fisher_yates_stream(pt, m, seed, (uint32_t)row, (uint32_t)((uint64_t)row >> 32),
+                        TAG_MASK, tmp);
+    for (int64_t t = 0; t < m; ++t) omega[t] = (int32_t)tmp[t];
+    free(tmp);
+}
+
+void oracle_init_rows(int64_t n, int64_t K, uint64_t seed, int64_t *rows) {
+    fisher_yates_stream(n, K, seed, 0u, 0u, TAG_INIT, rows);
+}
+
+/* ---------------- Walsh-Hadamard transform (Sec. III) ---------------- */
+
+/* In-place y <- H y with H the Sylvester-ordered Hadamard matrix scaled to
+ * be orthonormal, H[u][l] = (-1)^popcount(u & l) / sqrt(pt).  Textbook
+ * radix-2 butterflies followed by one scaling. */
+void oracle_fwht(double *y, int64_t pt) {
+    for (int64_t h = 1; h < pt; h *= 2) {
+        for (int64_t i = 0; i < pt; i += 2 * h) {
+            for (int64_t j = i; j < i + h; ++j) {
+                double a = y[j], b = y[j + h];
+                y[j] = a + b;
+                y[j + h] = a - b;
+            }
+        }
+    }
+    double scale = 1.0 / sqrt((double)pt);
+    for (int64_t j = 0; j < pt; ++j) y[j] *= scale;
+}
+
+/* y_i = H D [x_i; 0] for each row (Sec. III, Eq. (ROS); Algorithm 1, line
+ * "Y <- HDX"), zero-padding p -> pt.  Y is n x pt, row-major. */
+void oracle_precondition(const float *X, int64_t n, int64_t p, int64_t ldx,
+                         uint64_t seed, double *Y) {
+    int64_t pt = oracle_ptilde(p);
+    double *D = (double *)malloc((size_t)pt * sizeof(double));
+    oracle_signs(pt, seed, D);
+    for (int64_t i = 0; i < n; ++i) {
+        double *y = Y + i * pt;
+        for (int64_t j = 0; j < pt; ++j) {
+            double xj = (j < p) ? (double)X[i * ldx + j] : 0.0;
+            y[j] = D[j] * xj;
+        }
+        oracle_fwht(y, pt);
+    }
+    free(D);
+}
+
+/* Compression of rows row0..row0+n-1: w_i = R_i R_i^T y_i stored as ELL
+ * (idx[i][t] = Omega_r[t], val[i][t] = y_i[Omega_r[t]]), Algorithm 1. */
+void oracle_compress(const float *X, int64_t n, int64_t p, int64_t ldx, int64_t row0,
+                     int64_t m, uint64_t seed, int32_t *idx, double *val) {
+    int64_t pt = oracle_ptilde(p);
+    double *y = (double *)malloc((size_t)pt * sizeof(double));
+    double *D = (double *)malloc((size_t)pt * sizeof(double));
+    oracle_signs(pt, seed, D);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < pt; ++j)
+            y[j] = (j < p) ? D[j] * (double)X[i * ldx + j] : 0.0;
+        oracle_fwht(y, pt);
+        oracle_mask(pt, m, seed, row0 + i, idx + i * m);
+        for (int64_t t = 0; t < m; ++t) val[i * m + t] = y[idx[i * m + t]];
+    }
+    free(D);
+    free(y);
+}
+
+/* ---------------- Covariance estimator (Sec. V) ---------------- */
+
+/* G += sum_i w_i w_i^T, the unscaled sparse Gram of the ELL rows. */
+void oracle_gram(const int32_t *idx, const double *val, int64_t n, int64_t m, int64_t pt,
+                 double *G) {
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t *ix = idx + i * m;
+        const double *vx = val + i * m;
+        for (int64_t s = 0; s < m; ++s)
+            for (int64_t t = 0; t < m; ++t)
+                G[(int64_t)ix[s] * pt + ix[t]] += vx[s] * vx[t];
+    }
+}
+
+/* C_emp-hat = pt(pt-1)/(m(m-1)) * G / n; C_n = C_emp-hat - (pt-m)/(pt-1) diag(C_emp-hat)
+ * (Sec. V, definitions of C_emp-hat and C_n).  Requires m >= 2. */
+void oracle_cov_finalize(const double *G, int64_t n, int64_t m, int64_t pt, double *C) {
+    double P = (double)pt, M = (double)m;
+    double scale = P * (P - 1.0) / (M * (M - 1.0)) / (double)n;
+    for (int64_t a = 0; a < pt * pt; ++a) C[a] = scale * G[a];
+    double corr = (P - M) / (P - 1.0);
+    for (int64_t j = 0; j < pt; ++j) C[j * pt + j] -= corr * C[j * pt + j];
+}
+
+/* Sample-mean estimator (Sec. IV, Thm. "sampleMean"): (pt/m)(1/n) sum_i w_i. */
+void oracle_sample_mean(const int32_t *idx, const double *val, int64_t n, int64_t m,
+                        int64_t pt, double *mean) {
+    for (int64_t j = 0; j < pt; ++j) mean[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t t = 0; t < m; ++t) mean[idx[i * m + t]] += val[i * m + t];
+    double scale = (double)pt / (double)m / (double)n;
+    for (int64_t j = 0; j < pt; ++j) mean[j] *= scale;
+}
+
+/* ---------------- Sparsified K-means (Sec. VI-B) ---------------- */
+
+/* Eq. (assignments): c_i = argmin_k || z_i - R_i^T mu'_k ||^2, computed
+ * directly over the m sampled coordinates.  Ties go to the smallest k. */
+void oracle_kmeans_assign(const int32_t *idx, const double *val, int64_t n, int64_t m,
+                          const double *mu, int64_t K, int64_t pt, int32_t *labels,
+                          double *dist) {
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t best = 0;
+        double bestd = INFINITY;
+        for (int64_t k = 0; k < K; ++k) {
+            double d = 0.0;
+            for (int64_t t = 0; t < m; ++t) {
+                double diff = val[i * m + t] - mu[k * pt + idx[i * m + t]];
+                d += diff * diff;
+            }
+            if (d < bestd) { bestd = d; best = k; }
+        }
+        labels[i] = (int32_t)best;
+        if (dist) dist[i] = bestd;
+    }
+}
+
+/* Eq. (mu_update_one)/(mu_update_two): mu'_kj = S_kj / n_k^(j) with
+ * S_kj = sum over rows of cluster k that sampled j.  A coordinate that no
+ * row of the cluster sampled (n_k^(j) = 0) cannot be estimated; it keeps
+ * its previous value.  counts is K x pt, nk is K. */
+void oracle_kmeans_update(const int32_t *idx, const double *val, const int32_t *labels,
+                          int64_t n, int64_t m, int64_t K, int64_t pt,
+                          const double *mu_prev, double *mu_new, int64_t *counts,
+                          int64_t *nk) {
+    double *S = (double *)calloc((size_t)(K * pt), sizeof(double));
+    for (int64_t a = 0; a < K * pt; ++a) counts[a] = 0;
+    for (int64_t k = 0; k < K; ++k) nk[k] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = labels[i];
+        nk[k] += 1;
+        for (int64_t t = 0; t < m; ++t) {
+            int64_t j = idx[i * m + t];
+            S[k * pt + j] += val[i * m + t];
+            counts[k * pt + j] += 1;
+        }
+    }
+    for (int64_t a = 0; a < K * pt; ++a)
+        mu_new[a] = counts[a] > 0 ? S[a] / (double)counts[a] : mu_prev[a];
+    free(S);
+}
+
+/* Eq. (mu-mu'): mu = (HD)^T mu' = D H mu' (Sylvester H is symmetric),
+ * truncated to the first p coordinates.  in is r x pt, out is r x p. */
+void oracle_unmix(const double *in, int64_t r, int64_t pt, int64_t p, uint64_t seed,
+                  double *out) {
+    double *D = (double *)malloc((size_t)pt * sizeof(double));
+    double *y = (double *)malloc((size_t)pt * sizeof(double));
+    oracle_signs(pt, seed, D);
+    for (int64_t i = 0; i < r; ++i) {
+        memcpy(y, in + i * pt, (size_t)pt * sizeof(double));
+        oracle_fwht(y, pt);
+        for (int64_t j = 0; j < p; ++j) out[i * p + j] = D[j] * y[j];
+    }
+    free(D);
+    free(y);
+}

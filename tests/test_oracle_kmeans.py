@@ -1,0 +1,96 @@
+"""Pins for the oracle's sparsified K-means (Sec. VI-B, Algorithm 1).
+
+* m = p: J' reduces to the K-means objective on HDX and, HD being orthonormal,
+  the iterations are Lloyd's on X after un-mixing (Sec. VI-A).
+* Brute-force restricted distances on tiny inputs (Eq. (assignments)).
+* Coordinate descent: J' never increases (Sec. VI-B, steps 1 and 2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_00152_gb300 import synth
+
+
+def lloyd(X, C0, iters):
+    """Textbook Lloyd's iterations; empty clusters keep their centre."""
+    C = C0.copy()
+    labels = None
+    for _ in range(iters):
+        d = ((X[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+        labels = np.argmin(d, axis=1)
+        for k in range(C.shape[0]):
+            sel = labels == k
+            if sel.any():
+                C[k] = X[sel].mean(0)
+    return labels, C
+
+
+def test_full_sampling_reduces_to_lloyd():
+    n, p, K, seed = 300, 16, 4, 21
+    X, _, _ = synth.mixture(n, p, K, seed=5, heavy_frac=0.0)
+    pt = oracle.ptilde(p)
+    idx, val = oracle.compress(X, pt, seed)
+    rows = oracle.init_rows(n, K, seed)
+    Y = oracle.precondition(X, seed)
+    labels, mu, _ = oracle.kmeans(idx, val, Y[rows], pt, iters=6)
+    ref_labels, ref_C = lloyd(X.astype(np.float64), X[rows].astype(np.float64), 6)
+    # the oracle loop assigns then updates; the final labels are the ones the
+    # last update used, which matches lloyd's last assignment
+    assert np.array_equal(labels, ref_labels)
+    assert np.max(np.abs(oracle.unmix(mu, p, seed) - ref_C)) < 1e-11
+
+
+def test_assign_brute_force_and_ties():
+    rng = np.random.default_rng(4)
+    pt, m, n, K = 16, 5, 30, 6
+    idx = np.stack([rng.choice(pt, m, replace=False) for _ in range(n)]).astype(np.int32)
+    val = rng.standard_normal((n, m))
+    mu = rng.standard_normal((K, pt))
+    mu[3] = mu[1]  # exact duplicate centre: ties must resolve to k = 1
+    labels, dist = oracle.kmeans_assign(idx, val, mu, pt)
+    for i in range(n):
+        d = [sum((val[i, t] - mu[k, idx[i, t]]) ** 2 for t in range(m)) for k in range(K)]
+        best = int(np.argmin(d))  # numpy argmin returns the first minimum
+        assert labels[i] == best and labels[i] != 3
+        assert abs(dist[i] - d[best]) < 1e-12
+
+
+def test_assign_uses_restricted_norm():
+    """A centre with huge values on coordinates the row did not sample must
+    not be penalised (Eq. (assignments) only sees Omega_i)."""
+    pt = 8
+    idx = np.array([[0, 1]], np.int32)
+    val = np.array([[1.0, 1.0]])
+    mu = np.zeros((2, pt))
+    mu[0, :2] = 0.0
+    mu[1, :2] = 1.0
+    mu[1, 2:] = 1e6
+    labels, dist = oracle.kmeans_assign(idx, val, mu, pt)
+    assert labels[0] == 1 and dist[0] == 0.0
+
+
+def test_update_unsampled_and_empty_keep_previous():
+    pt, K = 8, 3
+    idx = np.array([[0, 1], [1, 2]], np.int32)
+    val = np.array([[2.0, 4.0], [6.0, 8.0]])
+    labels = np.array([0, 0], np.int32)
+    prev = np.arange(K * pt, dtype=np.float64).reshape(K, pt)
+    mu, counts, nk = oracle.kmeans_update(idx, val, labels, prev, pt)
+    assert mu[0, 0] == 2.0 and mu[0, 1] == 5.0 and mu[0, 2] == 8.0
+    assert np.array_equal(mu[0, 3:], prev[0, 3:])
+    assert np.array_equal(mu[1:], prev[1:])  # empty clusters unchanged
+    assert counts[0, 1] == 2 and nk.tolist() == [2, 0, 0]
+
+
+def test_objective_non_increasing_tiny_config():
+    n, p, m, K, seed = 2000, 64, 8, 5, 1
+    X = synth.lowrank_spiky(n, p, seed=seed)
+    pt = oracle.ptilde(p)
+    idx, val = oracle.compress(X, m, seed)
+    rows = oracle.init_rows(n, K, seed)
+    Y = oracle.precondition(X[rows], seed)
+    labels, mu, hist = oracle.kmeans(idx, val, Y, pt, iters=10)
+    # J' after each update is <= J' before it; the history records J' at each
+    # assignment, which can only go down
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(hist, hist[1:]))
