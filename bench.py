@@ -1,0 +1,440 @@
+#!/usr/bin/env python3
+"""Benchmark: samples/s of the whole hot path on one GB300 per rank.
+
+One step = one pass of every hot-path stage over the resident batch:
+  compress (H D x, mask draw, ELL)  ->  covariance (Gram accumulate, C_n
+  finalize)  ->  top-k PCA + un-mix  ->  K-means start (dense y of K seeded
+  rows)  ->  `iters` sparsified K-means iterations (one CUDA graph)  ->
+  un-mixed centres.
+Workload (default): n = 1,000,000, p = 1024, m = 51 (5%), K = 10, 20
+iterations; Gaussian mixture with centres N(0,1)*3, noise N(0, 0.5^2), 10% of
+rows Student-t(3) (synthetic, generated on the device from the seed).
+
+Multi-GPU: replicas only (the method needs no exchange on one GPU; each rank
+runs its own copy of the workload), "scaling": "weak".
+
+--impl reference times the CPU oracle (plain FP64 C) on a bounded row sample
+of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import os
+
+# the CPU oracle and numpy's LAPACK run single-threaded; say so in the output
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="kmeans_mixture_n1e6_p1024_m51_K10", n=1_000_000, p=1024, m=51, K=10,
+                iters=20, pca_k=10, seed=20240611)
+METRIC = "samples/s compress+cov+K-means iter at 1 GB300; %HBM/tensor peak; err vs FP64"
+UNIT = "samples/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(value: float, pg, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity on one rank)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device.index])
+        else:
+            pg.barrier()
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_step(X, cfg, rows_init):
+    """One step of the oracle on a row sample (compress, C_n, top-k, K-means)."""
+    import oracle
+    n, p = X.shape
+    m, K = cfg["m"], cfg["K"]
+    seed = cfg["seed"]
+    pt = oracle.ptilde(p)
+    idx, val = oracle.compress(X, m, seed)
+    C = oracle.cov(idx, val, pt)
+    w, V = oracle.pca_topk(C, cfg["pca_k"])
+    oracle.unmix(V.T.copy(), p, seed)
+    mu0 = oracle.precondition(X[rows_init], seed)
+    labels, mu, _ = oracle.kmeans(idx, val, mu0, pt, cfg["iters"])
+    oracle.unmix(mu, p, seed)
+    return labels
+
+
+def cpu_sample(cfg, rows: int):
+    from paper_1511_00152_gb300 import synth
+    X, _, _ = synth.mixture(rows, cfg["p"], cfg["K"], seed=cfg["seed"])
+    rows_init = synth.init_rows(rows, cfg["K"], cfg["seed"])
+    return X, rows_init
+
+
+def time_cpu_baseline(cfg, rows=4000):
+    X, ri = cpu_sample(cfg, rows)
+    oracle_step(X[:200], cfg, synth_rows(200, cfg))  # compile/warm the oracle
+    t = time.perf_counter()
+    oracle_step(X, cfg, ri)
+    dt = time.perf_counter() - t
+    return rows / dt, dt
+
+
+def synth_rows(n, cfg):
+    from paper_1511_00152_gb300 import synth
+    return synth.init_rows(n, cfg["K"], cfg["seed"])
+
+
+def run_reference(args, cfg):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    rows = args.ref_rows
+    X, ri = cpu_sample(cfg, rows)
+    for _ in range(args.warmup):
+        oracle_step(X, cfg, ri)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(X, cfg, ri)
+    dt = (time.perf_counter() - t) / args.steps
+    value = rows / dt
+    sample = (f"{rows} rows of the workload per step (full p, m, K, iters; compress, C_n, "
+              f"top-{cfg['pca_k']}, {cfg['iters']} K-means iterations)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {k: cfg[k] for k in ("workload", "n", "p", "m", "K", "iters")} | {"rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU path
+
+def run_gpu(args, cfg):
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1511_00152_gb300 import build as skbuild
+    skbuild.build()
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import pipeline, synth
+
+    n, p, m, K, iters, k = cfg["n"], cfg["p"], cfg["m"], cfg["K"], cfg["iters"], cfg["pca_k"]
+    seed = cfg["seed"] + rank
+    mode = {"fp32": sk.SK_GRAM_FP32, "bf16": sk.SK_GRAM_BF16, "bf16x3": sk.SK_GRAM_BF16X3}[args.gram]
+    ctx = sk.sk_init(p, m, seed)
+    pt = ctx.pt
+    X, _, _ = synth.mixture_device(n, p, 10, seed, device=dev)
+    rows = synth.init_rows(n, K, seed)
+    Xsel = X[torch.as_tensor(rows, device=dev)].contiguous()
+    idx = torch.empty((n, m), dtype=torch.int32, device=dev)
+    val = torch.empty((n, m), dtype=torch.float32, device=dev)
+    G = torch.empty((pt, pt), dtype=torch.float64, device=dev)
+    C = torch.empty((pt, pt), dtype=torch.float64, device=dev)
+    evals = torch.empty(k, dtype=torch.float64, device=dev)
+    U = torch.empty((k, pt), dtype=torch.float64, device=dev)
+    Ux = torch.empty((k, p), dtype=torch.float64, device=dev)
+    work = torch.empty(sk.sk_cov_topk_workspace(pt, k), dtype=torch.float64, device=dev)
+    cen = torch.empty((K, p), dtype=torch.float32, device=dev)
+    st = pipeline.KMeansState(ctx, n, K, device=dev)
+    stream = torch.cuda.current_stream()
+
+    stages = ["compress", "gram", "cov_finalize", "topk", "kmeans", "unmix"]
+    launches = {"compress": 1, "gram": 1, "cov_finalize": 1,
+                "topk": 1 + (args.topk_iters + 1) + 3 * args.topk_iters + 3 + 1,
+                "kmeans": 1 + 2 * iters, "unmix": 1}
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        sk.sk_compress(ctx, X, idx=idx, val=val)
+        mark(1)
+        sk.sk_cov_reset(ctx, G)
+        sk.sk_cov_accumulate(ctx, mode, idx, val, G)
+        mark(2)
+        sk.sk_cov_finalize(ctx, G, n, C=C)
+        mark(3)
+        sk.sk_cov_topk(ctx, C, k, args.topk_iters, evals=evals, U=U, work=work)
+        sk.sk_unmix(ctx, U, out=Ux)
+        mark(4)
+        sk.sk_precondition(ctx, Xsel, Y=st.mu)
+        st.graph.replay()
+        mark(5)
+        sk.sk_unmix(ctx, st.mu, out=cen)
+        mark(6)
+
+    # capture the K-means loop once (its own kernels, replayed as one graph)
+    mu0 = sk.sk_precondition(ctx, Xsel)
+    sk.sk_compress(ctx, X, idx=idx, val=val)
+    st.run(idx, val, mu0, iters, use_graph=True)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    t0.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    ms = max_over_ranks(ms, pg, dev)
+    stage_ms = {}
+    for i, name in enumerate(stages):
+        stage_ms[name] = sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
+    assert sk.sk_device_status() == sk.SK_OK
+
+    # ---- roofline of the dominant kernel
+    hbm, bf16, bf16s, peak_src = load_peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    kmeans_iter_ms = stage_ms["kmeans"] / iters
+    roof = None
+    if dom in ("compress", "kmeans"):
+        if dom == "compress":
+            bytes_ = n * (4 * p + 8 * m)
+            dur = stage_ms["compress"]
+            name = "compress_kernel<10,false>"
+        else:
+            bytes_ = n * (8 * m + 4 + 4)  # ELL read, label + dist write per iteration
+            dur = kmeans_iter_ms
+            name = "kmeans_kernel (fused assign+update, per iteration)"
+        ach = bytes_ / (dur * 1e-3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "algorithmic_bytes": bytes_,
+                "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
+    else:
+        ntile = (pt // 128) * (pt // 128 + 1) // 2 if args.gram == "fp32" else None
+        if args.gram == "fp32":
+            ops = n * m * m  # algorithmic products (FP32 scatter)
+            ach = ops / (stage_ms["gram"] * 1e-3) / 1e9
+            roof = {"kernel": "gram_fp32_kernel", "bound": "alu", "achieved": ach,
+                    "peak": None, "unit": "Gproducts/s", "frac": None, "traffic": None,
+                    "note": f"shared-memory atomic scatter over {ntile} tiles"}
+        else:
+            flops = 2.0 * n * pt * pt * (3 if args.gram == "bf16x3" else 1)
+            ach = flops / (stage_ms["gram"] * 1e-3) / 1e12
+            roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": ach,
+                    "peak": bf16s, "unit": "TFLOP/s", "frac": ach / bf16s, "traffic": None,
+                    "peak_source": f"{peak_src} bf16_tflops_sustained"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((n, p), dtype=torch.float32, pin_memory=True)
+        Xh.copy_(X)
+        lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        cen_h = torch.empty((K, p), dtype=torch.float32, pin_memory=True)
+        ux_h = torch.empty((k, p), dtype=torch.float64, pin_memory=True)
+        Xd2 = torch.empty_like(X)
+        Xsel2 = torch.empty_like(Xsel)
+        ridx = torch.as_tensor(rows, device=dev)
+
+        def e2e_step():
+            Xd2.copy_(Xh, non_blocking=True)
+            X_saved = X
+            sk.sk_compress(ctx, Xd2, idx=idx, val=val)
+            sk.sk_cov_reset(ctx, G)
+            sk.sk_cov_accumulate(ctx, mode, idx, val, G)
+            sk.sk_cov_finalize(ctx, G, n, C=C)
+            sk.sk_cov_topk(ctx, C, k, args.topk_iters, evals=evals, U=U, work=work)
+            sk.sk_unmix(ctx, U, out=Ux)
+            torch.index_select(Xd2, 0, ridx, out=Xsel2)
+            sk.sk_precondition(ctx, Xsel2, Y=st.mu)
+            st.graph.replay()
+            sk.sk_unmix(ctx, st.mu, out=cen)
+            lab_h.copy_(st.labels, non_blocking=True)
+            cen_h.copy_(cen, non_blocking=True)
+            ux_h.copy_(Ux, non_blocking=True)
+            del X_saved
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(pg, dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nst = max(1, min(args.steps, 5))
+        for _ in range(nst):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(a.elapsed_time(b) / nst, pg, dev)
+        e2e = {"value": world * n / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": n * p * 4,
+               "d2h_bytes_per_step": n * 4 + K * p * 4 + k * p * 8,
+               "ms_per_step": ems}
+        del Xh
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            v, dt = time_cpu_baseline(cfg, rows=args.cpu_rows)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_rows} rows of the workload (full p, m, K, iters), {dt:.1f} s"}
+        except Exception as exc:  # report, do not hide
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * n / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.gram == "fp32" else f"f32+{args.gram}",
+            "data": "synthetic",
+            "config": {"workload": cfg["workload"], "n": n, "p": p, "m": m, "K": K,
+                       "kmeans_iters": iters, "pca_k": k, "topk_iters": args.topk_iters,
+                       "gram": args.gram, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (X is 4.1 GB)"},
+            "stage_ms": stage_ms, "kmeans_iter_ms": kmeans_iter_ms,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": sum(launches.values()) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--gram", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--topk-iters", type=int, default=8)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--cpu-rows", type=int, default=4000)
+    ap.add_argument("--ref-rows", type=int, default=3000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    cfg = dict(WORKLOAD)
+    if args.n:
+        cfg["n"] = args.n
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_gpu(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * sk.h -- C ABI of the GB300 library for preconditioned data sparsification
+ * (Pourkamali-Anaraki & Becker, "Preconditioned Data Sparsification for Big
+ * Data with Applications to PCA and K-means").
+ *
+ * Conventions shared by every entry point:
+ *  - Samples are rows: X is n x p, row-major float32 with leading dimension
+ *    ldx >= p (the paper's p x n matrix with samples as columns, same bytes).
+ *  - pt ("p tilde") is the smallest power of two >= p.  Samples are
+ *    zero-padded to pt before the Walsh-Hadamard transform; all sampling
+ *    and rescaling uses pt in place of the paper's p.  Supported: 1 <= p <= 8192.
+ *  - Every pointer argument named as device memory must be device memory the
+ *    caller owns (for example torch storage); the library never frees it and
+ *    keeps no reference to it after the call returns.  Host pointers are
+ *    named as such.
+ *  - Every call that takes `stream` enqueues asynchronous work on that CUDA
+ *    stream (a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream) and returns without synchronising.
+ *  - Argument errors are found on the host before any launch and return
+ *    SK_EINVAL (or SK_EUNSUPPORTED for a valid but unsupported shape); nothing
+ *    is enqueued.  A CUDA launch error returns SK_ECUDA.  sk_last_error()
+ *    gives a message for the calling thread's most recent failure.
+ *  - Device-side waits in the library's own kernels are bounded; a wait that
+ *    runs out sets a device error word and the kernel returns early.
+ *    sk_device_status() reports (and clears) it as SK_ETIMEOUT.
+ *  - No call throws; no call allocates device memory except where stated.
+ *
+ * Random-number spec (bit-exact; the same text is implemented independently
+ * by the CPU oracle):  Philox4x32-10 (Salmon et al., SC'11) with key =
+ * (seed_lo, seed_hi).  Sign D_j = -1 iff bit (j mod 32) of word (j/32) mod 4
+ * of Philox(ctr = (j/128, 0, 0, 0x5349474E)) is set.  The mask of global row
+ * r draws words w = 0,1,... = word (w mod 4) of Philox(ctr = (w/4, r_lo,
+ * r_hi, 0x4D41534B)); U(s) is Lemire's multiply-shift with rejection; the
+ * mask is partial Fisher-Yates: for t = 0..m-1, k = t + U(pt - t), swap
+ * a[t], a[k] of the virtual identity array, emit a[t].
+ */
+#ifndef SK_H
+#define SK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sk_status {
+    SK_OK = 0,
+    SK_EINVAL = 1,        /* invalid argument (nothing enqueued) */
+    SK_ENOMEM = 2,        /* allocation refused */
+    SK_ECUDA = 3,         /* CUDA runtime or launch error */
+    SK_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+    SK_EUNSUPPORTED = 5   /* valid request outside the supported shapes */
+} sk_status;
+
+/* Gram precision modes for sk_cov_accumulate. */
+enum {
+    SK_GRAM_FP32 = 0,   /* FP32 products, shared-memory scatter, FP64 flush */
+    SK_GRAM_BF16 = 1,   /* BF16 x BF16 -> FP32 on tcgen05 tensor cores */
+    SK_GRAM_BF16X3 = 2  /* split-BF16 hi/lo, three tcgen05 products */
+};
+
+/* Opaque host-side handle: p, pt, m and the seed.  Holds no device memory. */
+typedef struct sk_ctx sk_ctx;
+
+/* Creates a handle for samples of dimension p keeping m of pt entries per
+ * sample, with all randomness keyed by seed.  The paper's problem statement
+ * (Sec. VI-B, Algorithm 1 input: X, K, gamma = m/p).  Requires 1 <= p <= 8192
+ * and 1 <= m <= pt.  *ctx receives the handle (host memory, freed by
+ * sk_destroy).  Returns SK_EINVAL / SK_EUNSUPPORTED / SK_ENOMEM. */
+sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed);
+
+/* Frees a handle from sk_init (NULL is ignored). */
+void sk_destroy(sk_ctx *ctx);
+
+/* pt of a handle, or -1 for NULL. */
+int64_t sk_ptilde(const sk_ctx *ctx);
+
+/* One-pass compression (Algorithm 1, lines "Y <- HDX" and "w_i = R_i R_i^T
+ * y_i"; Sec. III Eq. (ROS)): for local rows i = 0..n-1 with global row
+ * r = row0 + i, y_i = H D [x_i; 0] (orthonormal Sylvester H) and the ELL
+ * output keeps the m entries of the mask of row r in draw order:
+ *   idx[i*m + t] = Omega_r[t]  (int32, device, n*m),
+ *   val[i*m + t] = y_i[Omega_r[t]]  (float32, device, n*m).
+ * X: device, n x p with leading dimension ldx >= p.  row0 >= 0 lets a chunked
+ * stream reproduce a single call exactly.  n = 0 is a no-op. */
+sk_status sk_compress(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                      int64_t row0, int32_t *idx, float *val, void *stream);
+
+/* Dense preconditioning only (Sec. III, Eq. (ROS)): Y[i*pt + j] = (H D
+ * [x_i; 0])_j, Y device n x pt float32.  Used for K-means starting centres and
+ * the second pass of Algorithm 2. */
+sk_status sk_precondition(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                          float *Y, void *stream);
+
+/* Covariance accumulation (Sec. V): G += sum_i w_i w_i^T over the n ELL rows
+ * (idx, val as produced by sk_compress), w_i the pt-vector with val at idx.
+ * G: device float64 pt x pt, caller-zeroed before the first call; only its
+ * upper triangle (j <= k) is defined after the call, the strict lower
+ * triangle holds unspecified partial sums.  mode is SK_GRAM_*.  Repeated
+ * calls on chunks accumulate; the result does not depend on the chunking
+ * beyond floating-point summation order. */
+sk_status sk_cov_accumulate(const sk_ctx *ctx, int mode, const int32_t *idx,
+                            const float *val, int64_t n, double *G, void *stream);
+
+/* Zeroes a pt x pt float64 Gram accumulator G (device) on the stream. */
+sk_status sk_cov_reset(const sk_ctx *ctx, double *G, void *stream);
+
+/* Unbiased covariance estimate C_n (Sec. V): with P = pt,
+ *   C_emp-hat = P(P-1)/(m(m-1)) * G / n_total,
+ *   C_n = C_emp-hat - (P-m)/(P-1) diag(C_emp-hat),
+ * written as a full symmetric pt x pt float64 matrix C (device), reading the
+ * upper triangle of G (device).  Requires m >= 2 (Thm. B1) and n_total >= 1.
+ * G and C must not overlap. */
+sk_status sk_cov_finalize(const sk_ctx *ctx, const double *G, int64_t n_total,
+                          double *C, void *stream);
+
+/* Top-k principal subspace of the symmetric pt x pt estimate C (device
+ * float64), Sec. V PCA: eigenvalues (device float64, k, descending) and
+ * eigenvectors (device float64, pt x k column-major, i.e. vector c at
+ * U[c*pt .. c*pt+pt)) by block subspace iteration with Rayleigh-Ritz in
+ * float64 on the device.  iters bounds the iteration count; work is a device
+ * float64 scratch buffer of sk_cov_topk_workspace(pt, k) doubles.  Requires
+ * 1 <= k <= min(pt, 64). */
+sk_status sk_cov_topk(const sk_ctx *ctx, const double *C, int32_t k, int32_t iters,
+                      double *evals, double *U, double *work, void *stream);
+int64_t sk_cov_topk_workspace(int64_t pt, int32_t k);
+
+/* Sparsified K-means assignment (Sec. VI-B, Eq. (assignments)): for each
+ * ELL row i, labels[i] = argmin_k sum_t (val[i,t] - mu[k, idx[i,t]])^2 with
+ * ties going to the smallest k, the restricted squared distance computed
+ * directly in float32.  mu: device K x pt float32 (the preconditioned-domain
+ * centres mu').  labels: device int32 n.  dist: device float32 n or NULL
+ * (receives the winning distance).  1 <= K <= 256. */
+sk_status sk_kmeans_assign(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                           int64_t n, const float *mu, int32_t K, int32_t *labels,
+                           float *dist, void *stream);
+
+/* Sparsified K-means centre sums (Sec. VI-B, Eq. (mu_update_one)):
+ * accumulates S[k*pt + j] += sum of val over rows of cluster k that sampled
+ * j, cnt[k*pt + j] += n_k^(j) (how often j was sampled in cluster k) and
+ * nk[k] += rows in cluster k.  S: device float64 K x pt; cnt: device int32
+ * K x pt; nk: device int64 K; all caller-zeroed before the first call. */
+sk_status sk_kmeans_update(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                           const int32_t *labels, int64_t n, int32_t K, double *S,
+                           int32_t *cnt, int64_t *nk, void *stream);
+
+/* Fused one-pass iteration body: assignment against mu (as
+ * sk_kmeans_assign) and, in the same pass over the ELL rows, the sums of
+ * sk_kmeans_update under the new labels.  Same argument meanings. */
+sk_status sk_kmeans_step(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                         int64_t n, const float *mu, int32_t K, int32_t *labels,
+                         float *dist, double *S, int32_t *cnt, int64_t *nk,
+                         void *stream);
+
+/* Centre update (Eq. (mu_update_two)): mu[k*pt + j] = S/cnt where cnt > 0;
+ * a coordinate no row of cluster k sampled cannot be estimated and keeps its
+ * previous value (an empty cluster keeps its whole centre).  mu: device
+ * float32 K x pt, updated in place. */
+sk_status sk_kmeans_finalize(const sk_ctx *ctx, int32_t K, const double *S,
+                             const int32_t *cnt, float *mu, void *stream);
+
+/* Zeroes the K-means sums S (float64 K x pt), cnt (int32 K x pt) and nk
+ * (int64 K), all device, on the stream: the start of one accumulation pass. */
+sk_status sk_kmeans_reset(const sk_ctx *ctx, int32_t K, double *S, int32_t *cnt, int64_t *nk,
+                          void *stream);
+
+/* Un-mixing (Eq. (mu-mu'), Algorithm 1 last step): out_i = first p entries
+ * of (HD)^T in_i = D H in_i for r rows.  in: device float32 r x pt; out:
+ * device float32 r x p.  in and out must not overlap. */
+sk_status sk_unmix(const sk_ctx *ctx, const float *in, int64_t r, float *out,
+                   void *stream);
+
+/* float64 variant of sk_unmix (for eigenvectors): in r x pt, out r x p. */
+sk_status sk_unmix_f64(const sk_ctx *ctx, const double *in, int64_t r, double *out,
+                       void *stream);
+
+/* Reports SK_ETIMEOUT if a bounded device wait of this library ran out since
+ * the last call (and clears the flag), SK_ECUDA on a pending CUDA error, else
+ * SK_OK.  Synchronises the given stream first. */
+sk_status sk_device_status(void *stream);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char *sk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SK_H */

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of libsk.so (include/sk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Tensors are
+torch CUDA tensors (PyTorch provides the device memory and the stream);
+outputs the caller does not pass are allocated with torch.  All arithmetic
+runs in the library's CUDA kernels.  There is no fallback: if libsk.so is
+missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsk.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sk.h")
+
+SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = range(6)
+SK_GRAM_FP32, SK_GRAM_BF16, SK_GRAM_BF16X3 = 0, 1, 2
+STATUS_NAMES = {0: "SK_OK", 1: "SK_EINVAL", 2: "SK_ENOMEM", 3: "SK_ECUDA",
+                4: "SK_ETIMEOUT", 5: "SK_EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SkError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libsk.so (building it first only if explicitly asked by build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libsk.so not built at {p}; run paper_1511_00152_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        i64, i32, u64, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p
+        st = ctypes.c_int
+        sigs = {
+            "sk_init": (st, [ctypes.POINTER(vp), i64, i64, u64]),
+            "sk_destroy": (None, [vp]),
+            "sk_ptilde": (i64, [vp]),
+            "sk_compress": (st, [vp, vp, i64, i64, i64, vp, vp, vp]),
+            "sk_precondition": (st, [vp, vp, i64, i64, vp, vp]),
+            "sk_cov_accumulate": (st, [vp, ctypes.c_int, vp, vp, i64, vp, vp]),
+            "sk_cov_finalize": (st, [vp, vp, i64, vp, vp]),
+            "sk_cov_reset": (st, [vp, vp, vp]),
+            "sk_kmeans_reset": (st, [vp, i32, vp, vp, vp, vp]),
+            "sk_cov_topk": (st, [vp, vp, i32, i32, vp, vp, vp, vp]),
+            "sk_cov_topk_workspace": (i64, [i64, i32]),
+            "sk_kmeans_assign": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp]),
+            "sk_kmeans_update": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp]),
+            "sk_kmeans_step": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),
+            "sk_kmeans_finalize": (st, [vp, i32, vp, vp, vp, vp]),
+            "sk_unmix": (st, [vp, vp, i64, vp, vp]),
+            "sk_unmix_f64": (st, [vp, vp, i64, vp, vp]),
+            "sk_device_status": (st, [vp]),
+            "sk_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the entry points declared in include/sk.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sk_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(fn: str, status: int):
+    if status != SK_OK:
+        msg = load().sk_last_error()
+        raise SkError(fn, status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() and t.dim() != 2:
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Ctx:
+    """Owns an sk_ctx* (host memory only)."""
+
+    def __init__(self, handle: int, p: int, m: int, seed: int):
+        self._h = ctypes.c_void_p(handle)
+        self.p, self.m, self.seed = p, m, seed
+        self.pt = int(load().sk_ptilde(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.sk_destroy(self._h)
+                self._h = ctypes.c_void_p(0)
+        except Exception:
+            pass
+
+
+def sk_init(p: int, m: int, seed: int) -> Ctx:
+    h = ctypes.c_void_p(0)
+    _check("sk_init", load().sk_init(ctypes.byref(h), int(p), int(m), int(seed) & (2**64 - 1)))
+    return Ctx(h.value, int(p), int(m), int(seed))
+
+
+def sk_ptilde(ctx: Ctx) -> int:
+    return int(load().sk_ptilde(ctx.handle))
+
+
+def _rows_ld(X, p):
+    _need(X, torch.float32, "X")
+    if X.dim() != 2 or X.shape[1] != p or X.stride(1) != 1:
+        raise ValueError("X must be n x p with unit column stride")
+    return X.shape[0], X.stride(0) if X.shape[0] > 1 else p
+
+
+def sk_compress(ctx: Ctx, X, row0: int = 0, idx=None, val=None, stream=None):
+    n, ldx = _rows_ld(X, ctx.p)
+    dev = X.device
+    if idx is None:
+        idx = torch.empty((n, ctx.m), dtype=torch.int32, device=dev)
+    if val is None:
+        val = torch.empty((n, ctx.m), dtype=torch.float32, device=dev)
+    _need(idx, torch.int32, "idx", (n, ctx.m))
+    _need(val, torch.float32, "val", (n, ctx.m))
+    _check("sk_compress", load().sk_compress(ctx.handle, _ptr(X), n, ldx, int(row0), _ptr(idx),
+                                             _ptr(val), _stream(stream)))
+    return idx, val
+
+
+def sk_precondition(ctx: Ctx, X, Y=None, stream=None):
+    n, ldx = _rows_ld(X, ctx.p)
+    if Y is None:
+        Y = torch.empty((n, ctx.pt), dtype=torch.float32, device=X.device)
+    _need(Y, torch.float32, "Y", (n, ctx.pt))
+    _check("sk_precondition", load().sk_precondition(ctx.handle, _ptr(X), n, ldx, _ptr(Y),
+                                                     _stream(stream)))
+    return Y
+
+
+def sk_cov_accumulate(ctx: Ctx, mode: int, idx, val, G, stream=None):
+    n = idx.shape[0]
+    _need(idx, torch.int32, "idx", (n, ctx.m))
+    _need(val, torch.float32, "val", (n, ctx.m))
+    _need(G, torch.float64, "G", (ctx.pt, ctx.pt))
+    _check("sk_cov_accumulate", load().sk_cov_accumulate(ctx.handle, int(mode), _ptr(idx),
+                                                         _ptr(val), n, _ptr(G), _stream(stream)))
+    return G
+
+
+def sk_cov_reset(ctx: Ctx, G, stream=None):
+    _need(G, torch.float64, "G", (ctx.pt, ctx.pt))
+    _check("sk_cov_reset", load().sk_cov_reset(ctx.handle, _ptr(G), _stream(stream)))
+    return G
+
+
+def sk_kmeans_reset(ctx: Ctx, S, cnt, nk, stream=None):
+    K = nk.shape[0]
+    _need(S, torch.float64, "S", (K, ctx.pt))
+    _need(cnt, torch.int32, "cnt", (K, ctx.pt))
+    _need(nk, torch.int64, "nk", (K,))
+    _check("sk_kmeans_reset", load().sk_kmeans_reset(ctx.handle, K, _ptr(S), _ptr(cnt), _ptr(nk),
+                                                     _stream(stream)))
+    return S, cnt, nk
+
+
+def sk_cov_finalize(ctx: Ctx, G, n_total: int, C=None, stream=None):
+    _need(G, torch.float64, "G", (ctx.pt, ctx.pt))
+    if C is None:
+        C = torch.empty_like(G)
+    _need(C, torch.float64, "C", (ctx.pt, ctx.pt))
+    _check("sk_cov_finalize", load().sk_cov_finalize(ctx.handle, _ptr(G), int(n_total), _ptr(C),
+                                                     _stream(stream)))
+    return C
+
+
+def sk_cov_topk_workspace(pt: int, k: int) -> int:
+    return int(load().sk_cov_topk_workspace(int(pt), int(k)))
+
+
+def sk_cov_topk(ctx: Ctx, C, k: int, iters: int = 40, evals=None, U=None, work=None,
+                stream=None):
+    """Returns (evals descending [k], U [k, pt] with row c the c-th eigenvector)."""
+    _need(C, torch.float64, "C", (ctx.pt, ctx.pt))
+    dev = C.device
+    if evals is None:
+        evals = torch.empty(k, dtype=torch.float64, device=dev)
+    if U is None:
+        U = torch.empty((k, ctx.pt), dtype=torch.float64, device=dev)
+    if work is None:
+        ws = sk_cov_topk_workspace(ctx.pt, k)
+        if ws < 0:
+            raise SkError("sk_cov_topk_workspace", SK_EINVAL, "bad k")
+        work = torch.empty(ws, dtype=torch.float64, device=dev)
+    _check("sk_cov_topk", load().sk_cov_topk(ctx.handle, _ptr(C), int(k), int(iters), _ptr(evals),
+                                             _ptr(U), _ptr(work), _stream(stream)))
+    return evals, U
+
+
+def sk_kmeans_assign(ctx: Ctx, idx, val, mu, labels=None, dist=None, stream=None):
+    n = idx.shape[0]
+    K = mu.shape[0]
+    _need(mu, torch.float32, "mu", (K, ctx.pt))
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=idx.device)
+    _check("sk_kmeans_assign", load().sk_kmeans_assign(ctx.handle, _ptr(idx), _ptr(val), n,
+                                                       _ptr(mu), K, _ptr(labels), _ptr(dist),
+                                                       _stream(stream)))
+    return labels, dist
+
+
+def sk_kmeans_update(ctx: Ctx, idx, val, labels, K: int, S, cnt, nk, stream=None):
+    n = idx.shape[0]
+    _need(S, torch.float64, "S", (K, ctx.pt))
+    _need(cnt, torch.int32, "cnt", (K, ctx.pt))
+    _need(nk, torch.int64, "nk", (K,))
+    _check("sk_kmeans_update", load().sk_kmeans_update(ctx.handle, _ptr(idx), _ptr(val),
+                                                       _ptr(labels), n, int(K), _ptr(S),
+                                                       _ptr(cnt), _ptr(nk), _stream(stream)))
+    return S, cnt, nk
+
+
+def sk_kmeans_step(ctx: Ctx, idx, val, mu, labels, S, cnt, nk, dist=None, stream=None):
+    n = idx.shape[0]
+    K = mu.shape[0]
+    _check("sk_kmeans_step", load().sk_kmeans_step(ctx.handle, _ptr(idx), _ptr(val), n, _ptr(mu),
+                                                   K, _ptr(labels), _ptr(dist), _ptr(S),
+                                                   _ptr(cnt), _ptr(nk), _stream(stream)))
+    return labels
+
+
+def sk_kmeans_finalize(ctx: Ctx, S, cnt, mu, stream=None):
+    K = mu.shape[0]
+    _need(mu, torch.float32, "mu", (K, ctx.pt))
+    _check("sk_kmeans_finalize", load().sk_kmeans_finalize(ctx.handle, K, _ptr(S), _ptr(cnt),
+                                                           _ptr(mu), _stream(stream)))
+    return mu
+
+
+def sk_unmix(ctx: Ctx, M, out=None, stream=None):
+    r = M.shape[0]
+    if M.dtype == torch.float64:
+        if out is None:
+            out = torch.empty((r, ctx.p), dtype=torch.float64, device=M.device)
+        _check("sk_unmix_f64", load().sk_unmix_f64(ctx.handle, _ptr(M), r, _ptr(out),
+                                                   _stream(stream)))
+        return out
+    _need(M, torch.float32, "in", (r, ctx.pt))
+    if out is None:
+        out = torch.empty((r, ctx.p), dtype=torch.float32, device=M.device)
+    _check("sk_unmix", load().sk_unmix(ctx.handle, _ptr(M), r, _ptr(out), _stream(stream)))
+    return out
+
+
+def sk_device_status(stream=None) -> int:
+    """Returns the status code (SK_OK, SK_ETIMEOUT, SK_ECUDA) without raising."""
+    return int(load().sk_device_status(_stream(stream)))
+
+
+def sk_last_error() -> str:
+    msg = load().sk_last_error()
+    return msg.decode() if msg else ""

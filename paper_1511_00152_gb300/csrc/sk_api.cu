@@ -1,0 +1,264 @@
+// sk_api.cu -- the C ABI (include/sk.h): argument validation on the host,
+// then one or more kernel launches on the caller's stream.  No exception
+// crosses the boundary; every failure returns a status and records a message
+// for sk_last_error().
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sk_internal.cuh"
+
+namespace {
+
+thread_local char g_msg[512] = {0};
+
+sk_status fail(sk_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sk_status cuda_status(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) {
+        g_msg[0] = 0;
+        return SK_OK;
+    }
+    return fail(SK_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define SK_CHECK_CTX(c)                                                   \
+    do {                                                                  \
+        if (!(c)) return fail(SK_EINVAL, "%s: ctx is NULL", __func__);    \
+    } while (0)
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed) {
+    if (!ctx) return fail(SK_EINVAL, "sk_init: ctx out-pointer is NULL");
+    *ctx = nullptr;
+    if (p < 1) return fail(SK_EINVAL, "sk_init: p = %lld must be >= 1", (long long)p);
+    if (p > 8192) return fail(SK_EUNSUPPORTED, "sk_init: p = %lld > 8192", (long long)p);
+    int L = 0;
+    while ((1LL << L) < p) ++L;
+    const int64_t pt = 1LL << L;
+    if (m < 1 || m > pt)
+        return fail(SK_EINVAL, "sk_init: m = %lld must be in [1, pt = %lld]", (long long)m,
+                    (long long)pt);
+    sk_ctx *c = new (std::nothrow) sk_ctx;
+    if (!c) return fail(SK_ENOMEM, "sk_init: out of host memory");
+    c->p = p;
+    c->pt = pt;
+    c->log2pt = L;
+    c->m = m;
+    c->seed = seed;
+    *ctx = c;
+    g_msg[0] = 0;
+    return SK_OK;
+}
+
+void sk_destroy(sk_ctx *ctx) { delete ctx; }
+
+int64_t sk_ptilde(const sk_ctx *ctx) { return ctx ? ctx->pt : -1; }
+
+sk_status sk_compress(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx, int64_t row0,
+                      int32_t *idx, float *val, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 0) return fail(SK_EINVAL, "sk_compress: n < 0");
+    if (row0 < 0) return fail(SK_EINVAL, "sk_compress: row0 < 0");
+    if (ldx < ctx->p) return fail(SK_EINVAL, "sk_compress: ldx < p");
+    if (n == 0) return SK_OK;
+    if (!X || !idx || !val) return fail(SK_EINVAL, "sk_compress: NULL buffer");
+    return cuda_status(sk::launch_compress(*ctx, X, n, ldx, row0, idx, val, nullptr,
+                                           as_stream(stream)),
+                       "sk_compress");
+}
+
+sk_status sk_precondition(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx, float *Y,
+                          void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 0) return fail(SK_EINVAL, "sk_precondition: n < 0");
+    if (ldx < ctx->p) return fail(SK_EINVAL, "sk_precondition: ldx < p");
+    if (n == 0) return SK_OK;
+    if (!X || !Y) return fail(SK_EINVAL, "sk_precondition: NULL buffer");
+    return cuda_status(sk::launch_compress(*ctx, X, n, ldx, 0, nullptr, nullptr, Y,
+                                           as_stream(stream)),
+                       "sk_precondition");
+}
+
+sk_status sk_cov_accumulate(const sk_ctx *ctx, int mode, const int32_t *idx, const float *val,
+                            int64_t n, double *G, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 0) return fail(SK_EINVAL, "sk_cov_accumulate: n < 0");
+    if (mode != SK_GRAM_FP32 && mode != SK_GRAM_BF16 && mode != SK_GRAM_BF16X3)
+        return fail(SK_EINVAL, "sk_cov_accumulate: unknown mode %d", mode);
+    if (n == 0) return SK_OK;
+    if (!idx || !val || !G) return fail(SK_EINVAL, "sk_cov_accumulate: NULL buffer");
+    cudaError_t e;
+    if (mode == SK_GRAM_FP32) {
+        e = sk::launch_gram_fp32(*ctx, idx, val, n, G, as_stream(stream));
+    } else {
+        if (ctx->pt < 128)
+            return fail(SK_EUNSUPPORTED,
+                        "sk_cov_accumulate: tensor-core modes need pt >= 128 (pt = %lld)",
+                        (long long)ctx->pt);
+        e = sk::launch_gram_tc(*ctx, mode, idx, val, n, G, as_stream(stream));
+    }
+    return cuda_status(e, "sk_cov_accumulate");
+}
+
+sk_status sk_cov_reset(const sk_ctx *ctx, double *G, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (!G) return fail(SK_EINVAL, "sk_cov_reset: NULL buffer");
+    return cuda_status(cudaMemsetAsync(G, 0, (size_t)ctx->pt * ctx->pt * sizeof(double),
+                                       as_stream(stream)),
+                       "sk_cov_reset");
+}
+
+sk_status sk_cov_finalize(const sk_ctx *ctx, const double *G, int64_t n_total, double *C,
+                          void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (ctx->m < 2) return fail(SK_EINVAL, "sk_cov_finalize: needs m >= 2 (Thm. B1)");
+    if (n_total < 1) return fail(SK_EINVAL, "sk_cov_finalize: n_total < 1");
+    if (!G || !C) return fail(SK_EINVAL, "sk_cov_finalize: NULL buffer");
+    const size_t bytes = (size_t)ctx->pt * ctx->pt * sizeof(double);
+    if (overlaps(G, bytes, C, bytes)) return fail(SK_EINVAL, "sk_cov_finalize: G and C overlap");
+    return cuda_status(sk::launch_cov_finalize(*ctx, G, n_total, C, as_stream(stream)),
+                       "sk_cov_finalize");
+}
+
+int64_t sk_cov_topk_workspace(int64_t pt, int32_t k) {
+    if (pt < 1 || k < 1 || k > 64 || k > pt) return -1;
+    return sk::topk_workspace(pt, k);
+}
+
+sk_status sk_cov_topk(const sk_ctx *ctx, const double *C, int32_t k, int32_t iters,
+                      double *evals, double *U, double *work, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (k < 1 || k > 64 || k > ctx->pt)
+        return fail(SK_EINVAL, "sk_cov_topk: k = %d must be in [1, min(pt, 64)]", k);
+    if (iters < 0 || iters > 100000) return fail(SK_EINVAL, "sk_cov_topk: iters out of range");
+    if (!C || !evals || !U || !work) return fail(SK_EINVAL, "sk_cov_topk: NULL buffer");
+    return cuda_status(sk::launch_topk(*ctx, C, k, iters, evals, U, work, as_stream(stream)),
+                       "sk_cov_topk");
+}
+
+static sk_status kmeans_common(const char *fn, const sk_ctx *ctx, const int32_t *idx,
+                               const float *val, int64_t n, int32_t K) {
+    if (!ctx) return fail(SK_EINVAL, "%s: ctx is NULL", fn);
+    if (n < 0) return fail(SK_EINVAL, "%s: n < 0", fn);
+    if (K < 1 || K > 256) return fail(SK_EINVAL, "%s: K = %d must be in [1, 256]", fn, K);
+    if (n > 0 && (!idx || !val)) return fail(SK_EINVAL, "%s: NULL ELL buffer", fn);
+    if ((int64_t)K * ctx->pt > (1LL << 31) - 1) return fail(SK_EUNSUPPORTED, "%s: K*pt too big", fn);
+    return SK_OK;
+}
+
+sk_status sk_kmeans_assign(const sk_ctx *ctx, const int32_t *idx, const float *val, int64_t n,
+                           const float *mu, int32_t K, int32_t *labels, float *dist,
+                           void *stream) {
+    sk_status st = kmeans_common("sk_kmeans_assign", ctx, idx, val, n, K);
+    if (st != SK_OK) return st;
+    if (n == 0) return SK_OK;
+    if (!mu || !labels) return fail(SK_EINVAL, "sk_kmeans_assign: NULL buffer");
+    return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, mu, K, labels, dist, nullptr,
+                                         nullptr, nullptr, true, false, as_stream(stream)),
+                       "sk_kmeans_assign");
+}
+
+sk_status sk_kmeans_update(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                           const int32_t *labels, int64_t n, int32_t K, double *S, int32_t *cnt,
+                           int64_t *nk, void *stream) {
+    sk_status st = kmeans_common("sk_kmeans_update", ctx, idx, val, n, K);
+    if (st != SK_OK) return st;
+    if (n == 0) return SK_OK;
+    if (!labels || !S || !cnt || !nk) return fail(SK_EINVAL, "sk_kmeans_update: NULL buffer");
+    return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, nullptr, K,
+                                         const_cast<int32_t *>(labels), nullptr, S, cnt, nk,
+                                         false, true, as_stream(stream)),
+                       "sk_kmeans_update");
+}
+
+sk_status sk_kmeans_step(const sk_ctx *ctx, const int32_t *idx, const float *val, int64_t n,
+                         const float *mu, int32_t K, int32_t *labels, float *dist, double *S,
+                         int32_t *cnt, int64_t *nk, void *stream) {
+    sk_status st = kmeans_common("sk_kmeans_step", ctx, idx, val, n, K);
+    if (st != SK_OK) return st;
+    if (n == 0) return SK_OK;
+    if (!mu || !labels || !S || !cnt || !nk) return fail(SK_EINVAL, "sk_kmeans_step: NULL buffer");
+    return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, mu, K, labels, dist, S, cnt, nk, true,
+                                         true, as_stream(stream)),
+                       "sk_kmeans_step");
+}
+
+sk_status sk_kmeans_finalize(const sk_ctx *ctx, int32_t K, const double *S, const int32_t *cnt,
+                             float *mu, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (K < 1 || K > 256) return fail(SK_EINVAL, "sk_kmeans_finalize: K out of range");
+    if (!S || !cnt || !mu) return fail(SK_EINVAL, "sk_kmeans_finalize: NULL buffer");
+    return cuda_status(sk::launch_kmeans_finalize(*ctx, K, S, cnt, mu, as_stream(stream)),
+                       "sk_kmeans_finalize");
+}
+
+sk_status sk_kmeans_reset(const sk_ctx *ctx, int32_t K, double *S, int32_t *cnt, int64_t *nk,
+                          void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (K < 1 || K > 256) return fail(SK_EINVAL, "sk_kmeans_reset: K out of range");
+    if (!S || !cnt || !nk) return fail(SK_EINVAL, "sk_kmeans_reset: NULL buffer");
+    const size_t KP = (size_t)K * ctx->pt;
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemsetAsync(S, 0, KP * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, KP * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nk, 0, (size_t)K * sizeof(int64_t), s);
+    return cuda_status(e, "sk_kmeans_reset");
+}
+
+sk_status sk_unmix(const sk_ctx *ctx, const float *in, int64_t r, float *out, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (r < 0) return fail(SK_EINVAL, "sk_unmix: r < 0");
+    if (r == 0) return SK_OK;
+    if (!in || !out) return fail(SK_EINVAL, "sk_unmix: NULL buffer");
+    if (overlaps(in, (size_t)r * ctx->pt * 4, out, (size_t)r * ctx->p * 4))
+        return fail(SK_EINVAL, "sk_unmix: in and out overlap");
+    return cuda_status(sk::launch_unmix(*ctx, in, r, out, false, as_stream(stream)), "sk_unmix");
+}
+
+sk_status sk_unmix_f64(const sk_ctx *ctx, const double *in, int64_t r, double *out,
+                       void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (r < 0) return fail(SK_EINVAL, "sk_unmix_f64: r < 0");
+    if (r == 0) return SK_OK;
+    if (!in || !out) return fail(SK_EINVAL, "sk_unmix_f64: NULL buffer");
+    if (overlaps(in, (size_t)r * ctx->pt * 8, out, (size_t)r * ctx->p * 8))
+        return fail(SK_EINVAL, "sk_unmix_f64: in and out overlap");
+    return cuda_status(sk::launch_unmix(*ctx, in, r, out, true, as_stream(stream)),
+                       "sk_unmix_f64");
+}
+
+sk_status sk_device_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return cuda_status(e, "sk_device_status");
+    unsigned int flag = 0;
+    e = sk::take_device_error(&flag);
+    if (e != cudaSuccess) return cuda_status(e, "sk_device_status");
+    if (flag) {
+        return fail(SK_ETIMEOUT, "sk_device_status: a bounded device wait ran out (flag 0x%x)",
+                    flag);
+    }
+    g_msg[0] = 0;
+    return SK_OK;
+}
+
+const char *sk_last_error(void) { return g_msg; }
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// sk_internal.cuh -- device helpers shared by the library's kernels.
+//
+// Philox4x32-10 follows Salmon, Moraes, Dror and Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64-bit
+// multiplies with the Weyl key schedule.  The word layout of the sign and
+// mask streams is the library's written spec (see include/sk.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sk.h"
+
+namespace sk {
+
+constexpr uint32_t kTagSign = 0x5349474Eu;  // "SIGN"
+constexpr uint32_t kTagMask = 0x4D41534Bu;  // "MASK"
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+        const uint32_t lo1 = kPhiloxM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t pick_word(uint4 v, uint32_t lane) {
+    return lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
+}
+
+// Word w of the mask stream of global row g.
+__device__ __forceinline__ uint32_t mask_word(uint32_t k0, uint32_t k1, uint64_t g,
+                                              uint32_t w) {
+    const uint4 o = philox4x32_10(
+        make_uint4(w >> 2, (uint32_t)g, (uint32_t)(g >> 32), kTagMask), k0, k1);
+    return pick_word(o, w & 3u);
+}
+
+// Sign bit (1 = negative) of coordinate j of D.
+__device__ __forceinline__ uint32_t sign_bit(uint32_t k0, uint32_t k1, uint32_t j) {
+    const uint4 o = philox4x32_10(make_uint4(j >> 7, 0u, 0u, kTagSign), k0, k1);
+    return (pick_word(o, (j >> 5) & 3u) >> (j & 31u)) & 1u;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned lanemask_gt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_gt;" : "=r"(r));
+    return r;
+}
+
+}  // namespace sk
+
+// Host-side launchers (defined in the kernel files, called by sk_api.cu).
+struct sk_ctx {
+    int64_t p;
+    int64_t pt;
+    int log2pt;
+    int64_t m;
+    uint64_t seed;
+};
+
+namespace sk {
+cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                            int64_t row0, int32_t *idx, float *val, float *Y,
+                            cudaStream_t s);
+cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
+                          int64_t n, const float *mu, int K, int32_t *labels, float *dist,
+                          double *S, int32_t *cnt, int64_t *nk, bool do_assign,
+                          bool do_update, cudaStream_t s);
+cudaError_t launch_kmeans_finalize(const sk_ctx &c, int K, const double *S,
+                                   const int32_t *cnt, float *mu, cudaStream_t s);
+cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *val,
+                             int64_t n, double *G, cudaStream_t s);
+cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx,
+                           const float *val, int64_t n, double *G, cudaStream_t s);
+cudaError_t launch_cov_finalize(const sk_ctx &c, const double *G, int64_t n_total,
+                                double *C, cudaStream_t s);
+cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out,
+                         bool f64, cudaStream_t s);
+cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters,
+                        double *evals, double *U, double *work, cudaStream_t s);
+int64_t topk_workspace(int64_t pt, int k);
+// Reads and clears the device error word of the kernels with bounded waits
+// (bit 0: an mbarrier wait ran out).  Returns cudaSuccess or the copy error.
+cudaError_t take_device_error(unsigned int *flag);
+}  // namespace sk

@@ -1,0 +1,328 @@
+// topk.cu -- top-k principal subspace of the symmetric pt x pt estimate C_n
+// (Sec. V: PCA recovers the leading eigenvectors of the covariance), in
+// float64 on the device.
+//
+// Block subspace iteration with b = min(pt, 64, max(k + 8, 2k)) columns:
+//   W = C V;  V = W R^{-1} with R the Cholesky factor of W^T W (CholQR),
+// repeated `iters` times from a seeded start, then one Rayleigh-Ritz step:
+// H = V^T C V (b x b), H = Q diag(lambda) Q^T by cyclic Jacobi rotations, and
+// U = V Q restricted to the k largest lambda.  Each eigenvector's sign makes
+// its largest-magnitude entry positive.  Everything is float64: the panel
+// product is a tiled CUDA-core kernel, the small b x b factorisations run in
+// one CTA.
+#include "sk_internal.cuh"
+
+namespace sk {
+namespace {
+
+constexpr int kMaxB = 64;
+constexpr uint32_t kTagTopk = 0x544F504Bu;  // "TOPK"
+
+int block_cols(int64_t pt, int k) {
+    int b = 2 * k > k + 8 ? 2 * k : k + 8;
+    if (b > kMaxB) b = kMaxB;
+    if (b > pt) b = (int)pt;
+    if (b < k) b = k;
+    return b;
+}
+
+// Workspace layout (doubles): V[b*pt] W[b*pt] Gm[b*b] Rinv[b*b] H[b*b] Q[b*b] lam[b]
+struct Ws {
+    double *V, *W, *Gm, *Rinv, *H, *Q, *lam;
+};
+Ws carve(double *work, int64_t pt, int b) {
+    Ws w;
+    w.V = work;
+    w.W = w.V + (int64_t)b * pt;
+    w.Gm = w.W + (int64_t)b * pt;
+    w.Rinv = w.Gm + b * b;
+    w.H = w.Rinv + b * b;
+    w.Q = w.H + b * b;
+    w.lam = w.Q + b * b;
+    return w;
+}
+
+__global__ void init_v_kernel(double *V, int64_t pt, int b, uint32_t k0, uint32_t k1) {
+    const int64_t total = (int64_t)b * pt;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)(e >> 32), 0u, kTagTopk),
+                                      k0, k1);
+        V[e] = ((double)o.x + 0.5) * (1.0 / 4294967296.0) - 0.5;
+    }
+}
+
+// W[c*pt + i] = sum_j C[i*pt + j] * V[c*pt + j] for c < b.  CTA: 64 rows i.
+__global__ void __launch_bounds__(256) panel_kernel(const double *C, const double *V,
+                                                    int64_t pt, int b, double *W) {
+    __shared__ double Cs[64][33];
+    __shared__ double Vs[kMaxB][33];
+    const int tid = threadIdx.x;
+    const int ri = tid & 63, cg = tid >> 6;  // 4 column groups
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
+    double acc[kMaxB / 4];
+#pragma unroll
+    for (int q = 0; q < kMaxB / 4; ++q) acc[q] = 0.0;
+    for (int64_t j0 = 0; j0 < pt; j0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e >> 5, cc = e & 31;
+            const int64_t gi = i0 + r, gj = j0 + cc;
+            Cs[r][cc] = (gi < pt && gj < pt) ? C[gi * pt + gj] : 0.0;
+        }
+        for (int e = tid; e < b * 32; e += 256) {
+            const int c = e >> 5, cc = e & 31;
+            const int64_t gj = j0 + cc;
+            Vs[c][cc] = (gj < pt) ? V[(int64_t)c * pt + gj] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int cc = 0; cc < 32; ++cc) {
+            const double cv = Cs[ri][cc];
+#pragma unroll
+            for (int q = 0; q < kMaxB / 4; ++q) {
+                const int c = cg + 4 * q;
+                if (c < b) acc[q] = fma(cv, Vs[c][cc], acc[q]);
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t gi = i0 + ri;
+    if (gi < pt) {
+#pragma unroll
+        for (int q = 0; q < kMaxB / 4; ++q) {
+            const int c = cg + 4 * q;
+            if (c < b) W[(int64_t)c * pt + gi] = acc[q];
+        }
+    }
+}
+
+// Gm[c1*b + c2] = A[c1]^T B[c2] over pt (one CTA per (c1, c2)).
+__global__ void small_gram_kernel(const double *A, const double *B, int64_t pt, int b,
+                                  double *Gm) {
+    __shared__ double red[256];
+    const int c1 = blockIdx.x / b, c2 = blockIdx.x % b;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < pt; i += blockDim.x)
+        s = fma(A[(int64_t)c1 * pt + i], B[(int64_t)c2 * pt + i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) Gm[blockIdx.x] = red[0];
+}
+
+// Cholesky Gm = R^T R (upper R) and Rinv = R^{-1}, one CTA.  A pivot that is
+// not safely positive (rank-deficient block) is replaced by a tiny positive
+// value so the column is kept and re-normalised in later iterations.
+__global__ void chol_inv_kernel(const double *Gm, int b, double *Rinv) {
+    __shared__ double R[kMaxB][kMaxB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        R[e / b][e % b] = Gm[e];
+        Rinv[e] = 0.0;
+    }
+    __syncthreads();
+    double trace = 0.0;
+    for (int c = 0; c < b; ++c) trace += R[c][c];
+    const double floor_v = 1e-300 + 1e-28 * trace;
+    for (int c = 0; c < b; ++c) {
+        if (tid == 0) {
+            double d = R[c][c];
+            for (int q = 0; q < c; ++q) d -= R[q][c] * R[q][c];
+            R[c][c] = sqrt(d > floor_v ? d : floor_v);
+        }
+        __syncthreads();
+        for (int j = c + 1 + tid; j < b; j += blockDim.x) {
+            double s = R[c][j];
+            for (int q = 0; q < c; ++q) s -= R[q][c] * R[q][j];
+            R[c][j] = s / R[c][c];
+        }
+        __syncthreads();
+    }
+    // inverse of upper-triangular R, column by column (a thread per column;
+    // each thread reads and writes only its own column of Rinv)
+    for (int j = tid; j < b; j += blockDim.x) {
+        for (int i = j; i >= 0; --i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int q = i + 1; q <= j; ++q) s -= R[i][q] * Rinv[q * b + j];
+            Rinv[i * b + j] = s / R[i][i];
+        }
+    }
+}
+
+// V[c*pt + i] = sum_{q <= c} W[q*pt + i] * Rinv[q*b + c]
+__global__ void apply_rinv_kernel(const double *W, const double *Rinv, int64_t pt, int b,
+                                  double *V) {
+    __shared__ double Rs[kMaxB * kMaxB];
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = Rinv[e];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double w[kMaxB];
+        for (int q = 0; q < b; ++q) w[q] = W[(int64_t)q * pt + i];
+        for (int c = 0; c < b; ++c) {
+            double s = 0.0;
+            for (int q = 0; q <= c; ++q) s = fma(w[q], Rs[q * b + c], s);
+            V[(int64_t)c * pt + i] = s;
+        }
+    }
+}
+
+// Cyclic Jacobi eigen-decomposition of the symmetric b x b H (one CTA):
+// H = Q diag(lam) Q^T.
+__global__ void jacobi_kernel(const double *Hin, int b, double *Q, double *lam) {
+    __shared__ double A[kMaxB][kMaxB + 1];
+    __shared__ double cs[2];
+    __shared__ int done;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        const int r = e / b, c = e % b;
+        A[r][c] = 0.5 * (Hin[r * b + c] + Hin[c * b + r]);
+    }
+    // Q (global) accumulates the rotations; thread r owns row r of Q.
+    for (int r = tid; r < b; r += blockDim.x)
+        for (int c = 0; c < b; ++c) Q[r * b + c] = (r == c) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        if (tid == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int r = 0; r < b; ++r)
+                for (int c = 0; c < b; ++c) {
+                    tot += A[r][c] * A[r][c];
+                    if (r != c) off += A[r][c] * A[r][c];
+                }
+            done = off <= 1e-30 * tot || tot == 0.0;
+        }
+        __syncthreads();
+        if (done) break;
+        for (int pp = 0; pp < b - 1; ++pp) {
+            for (int qq = pp + 1; qq < b; ++qq) {
+                if (tid == 0) {
+                    const double apq = A[pp][qq];
+                    double c = 1.0, s = 0.0;
+                    if (apq != 0.0) {
+                        const double theta = (A[qq][qq] - A[pp][pp]) / (2.0 * apq);
+                        const double t = (theta >= 0 ? 1.0 : -1.0) /
+                                         (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    }
+                    cs[0] = c;
+                    cs[1] = s;
+                }
+                __syncthreads();
+                const double c = cs[0], s = cs[1];
+                if (s != 0.0) {
+                    // A <- J^T A J with J the rotation in the (pp, qq) plane
+                    for (int r = tid; r < b; r += blockDim.x) {
+                        const double arp = A[r][pp], arq = A[r][qq];
+                        A[r][pp] = c * arp - s * arq;
+                        A[r][qq] = s * arp + c * arq;
+                    }
+                    __syncthreads();
+                    for (int r = tid; r < b; r += blockDim.x) {
+                        const double apr = A[pp][r], aqr = A[qq][r];
+                        A[pp][r] = c * apr - s * aqr;
+                        A[qq][r] = s * apr + c * aqr;
+                        const double vrp = Q[r * b + pp], vrq = Q[r * b + qq];
+                        Q[r * b + pp] = c * vrp - s * vrq;
+                        Q[r * b + qq] = s * vrp + c * vrq;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int r = tid; r < b; r += blockDim.x) lam[r] = A[r][r];
+}
+
+// U[c*pt + i] = sum_q V[q*pt + i] Q[q*b + order[c]] for the k largest lambda,
+// then the sign convention.  One CTA per output column c.
+__global__ void ritz_out_kernel(const double *V, const double *Q, const double *lam,
+                                int64_t pt, int b, int k, double *U, double *evals) {
+    __shared__ int order_c;
+    __shared__ double red_v[256];
+    __shared__ int64_t red_i[256];
+    const int c = blockIdx.x;
+    if (threadIdx.x == 0) {
+        // c-th largest eigenvalue (ties by lower index)
+        bool used[kMaxB];
+        for (int q = 0; q < b; ++q) used[q] = false;
+        int pick = 0;
+        for (int r = 0; r <= c; ++r) {
+            pick = -1;
+            for (int q = 0; q < b; ++q)
+                if (!used[q] && (pick < 0 || lam[q] > lam[pick])) pick = q;
+            used[pick] = true;
+        }
+        order_c = pick;
+        evals[c] = lam[pick];
+    }
+    __syncthreads();
+    const int col = order_c;
+    double best = -1.0;
+    int64_t besti = 0;
+    for (int64_t i = threadIdx.x; i < pt; i += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < b; ++q) s = fma(V[(int64_t)q * pt + i], Q[q * b + col], s);
+        U[(int64_t)c * pt + i] = s;
+        if (fabs(s) > best) {
+            best = fabs(s);
+            besti = i;
+        }
+    }
+    red_v[threadIdx.x] = best;
+    red_i[threadIdx.x] = besti;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            const double ov = red_v[threadIdx.x + h];
+            const int64_t oi = red_i[threadIdx.x + h];
+            if (ov > red_v[threadIdx.x] || (ov == red_v[threadIdx.x] && oi < red_i[threadIdx.x])) {
+                red_v[threadIdx.x] = ov;
+                red_i[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const bool flip = U[(int64_t)c * pt + red_i[0]] < 0.0;
+    __syncthreads();
+    if (flip)
+        for (int64_t i = threadIdx.x; i < pt; i += blockDim.x) U[(int64_t)c * pt + i] *= -1.0;
+}
+
+}  // namespace
+
+int64_t topk_workspace(int64_t pt, int k) {
+    const int b = block_cols(pt, k);
+    return 2 * (int64_t)b * pt + 4 * (int64_t)b * b + b;
+}
+
+cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, double *evals,
+                        double *U, double *work, cudaStream_t s) {
+    const int64_t pt = c.pt;
+    const int b = block_cols(pt, k);
+    Ws w = carve(work, pt, b);
+    const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
+    const int pblocks = (int)((pt + 63) / 64);
+    int eblocks = (int)((b * pt + 255) / 256);
+    if (eblocks > 4096) eblocks = 4096;
+    int ablocks = (int)((pt + 127) / 128);
+    init_v_kernel<<<eblocks, 256, 0, s>>>(w.V, pt, b, k0, k1);
+    for (int it = 0; it <= iters; ++it) {
+        panel_kernel<<<pblocks, 256, 0, s>>>(C, w.V, pt, b, w.W);
+        if (it == iters) break;
+        small_gram_kernel<<<b * b, 256, 0, s>>>(w.W, w.W, pt, b, w.Gm);
+        chol_inv_kernel<<<1, 64, 0, s>>>(w.Gm, b, w.Rinv);
+        apply_rinv_kernel<<<ablocks, 128, 0, s>>>(w.W, w.Rinv, pt, b, w.V);
+    }
+    // Rayleigh-Ritz: H = V^T (C V)
+    small_gram_kernel<<<b * b, 256, 0, s>>>(w.V, w.W, pt, b, w.H);
+    jacobi_kernel<<<1, 64, 0, s>>>(w.H, b, w.Q, w.lam);
+    ritz_out_kernel<<<k, 256, 0, s>>>(w.V, w.Q, w.lam, pt, b, k, U, evals);
+    return cudaGetLastError();
+}
+
+}  // namespace sk

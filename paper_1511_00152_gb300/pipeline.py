@@ -1,0 +1,84 @@
+"""Host-side drivers of the paper's algorithms over the C ABI.
+
+Only control flow lives here (loops, buffer management, CUDA-graph capture);
+every arithmetic step is a libsk.so kernel reached through ``_lib``.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as sk
+
+
+class KMeansState:
+    """Device buffers of one sparsified K-means run (Algorithm 1 loop)."""
+
+    def __init__(self, ctx: sk.Ctx, n: int, K: int, device="cuda"):
+        self.ctx, self.n, self.K = ctx, n, K
+        self.mu = torch.empty((K, ctx.pt), dtype=torch.float32, device=device)
+        self.labels = torch.empty(n, dtype=torch.int32, device=device)
+        self.dist = torch.empty(n, dtype=torch.float32, device=device)
+        self.S = torch.empty((K, ctx.pt), dtype=torch.float64, device=device)
+        self.cnt = torch.empty((K, ctx.pt), dtype=torch.int32, device=device)
+        self.nk = torch.empty(K, dtype=torch.int64, device=device)
+        self.graph = None
+        self._graph_args = None
+
+    def iteration(self, idx, val, stream=None):
+        """One assign + update pass (Eqs. (assignments), (mu_update_two))."""
+        ctx = self.ctx
+        sk.sk_kmeans_reset(ctx, self.S, self.cnt, self.nk, stream=stream)
+        sk.sk_kmeans_step(ctx, idx, val, self.mu, self.labels, self.S, self.cnt, self.nk,
+                          dist=self.dist, stream=stream)
+        sk.sk_kmeans_finalize(ctx, self.S, self.cnt, self.mu, stream=stream)
+
+    def run(self, idx, val, mu0, iters: int, use_graph: bool = True):
+        """iters iterations from the preconditioned-domain centres mu0 (K x pt).
+
+        With use_graph, the loop is captured once as a CUDA graph and replayed
+        (the same kernels, one launch for the whole loop)."""
+        self.mu.copy_(mu0)
+        if not use_graph or iters == 0:
+            for _ in range(iters):
+                self.iteration(idx, val)
+            return self.labels, self.mu
+        key = (idx.data_ptr(), val.data_ptr(), idx.shape[0], iters)
+        if self.graph is None or self._graph_args != key:
+            # warm the launch configuration outside capture, then capture
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                saved = self.mu.clone()
+                self.iteration(idx, val, stream=s)
+                self.mu.copy_(saved)
+            torch.cuda.current_stream().wait_stream(s)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                for _ in range(iters):
+                    self.iteration(idx, val)
+            self.graph, self._graph_args = g, key
+            self.mu.copy_(mu0)
+        self.graph.replay()
+        return self.labels, self.mu
+
+
+def initial_centres(ctx: sk.Ctx, X, rows) -> torch.Tensor:
+    """Preconditioned rows X[rows] (dense y = H D x) as starting centres."""
+    sel = X[torch.as_tensor(rows, device=X.device, dtype=torch.long)].contiguous()
+    return sk.sk_precondition(ctx, sel)
+
+
+def covariance(ctx: sk.Ctx, idx, val, mode: int, G=None, C=None):
+    """C_n from one batch of ELL rows (Sec. V)."""
+    if G is None:
+        G = torch.empty((ctx.pt, ctx.pt), dtype=torch.float64, device=idx.device)
+    sk.sk_cov_reset(ctx, G)
+    sk.sk_cov_accumulate(ctx, mode, idx, val, G)
+    return sk.sk_cov_finalize(ctx, G, idx.shape[0], C=C)
+
+
+def pca(ctx: sk.Ctx, C, k: int, iters: int = 40):
+    """Top-k eigenpairs of C_n and the eigenvectors un-mixed to the data domain
+    (U = (HD)^T U', Sec. V).  Returns (evals, U' [k x pt], U [k x p])."""
+    evals, Up = sk.sk_cov_topk(ctx, C, k, iters)
+    return evals, Up, sk.sk_unmix(ctx, Up)

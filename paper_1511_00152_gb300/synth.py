@@ -136,3 +136,10 @@ def lowrank_spiky_device(n: int, p: int, seed: int, sv=(10.0, 6.0, 4.0, 2.0, 1.0
     rows = torch.nonzero(spiky).flatten()
     X[rows, cols[rows]] *= spike
     return X.contiguous()
+
+
+def init_rows(n: int, K: int, seed: int) -> np.ndarray:
+    """K distinct row indices of [0, n) for a seeded K-means start (the same
+    rows go to the CUDA path and to the oracle)."""
+    rng = np.random.default_rng([int(seed), 0x494E4954])
+    return np.sort(rng.choice(n, size=K, replace=False)).astype(np.int64)

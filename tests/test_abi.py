@@ -1,0 +1,45 @@
+"""The C-ABI library loads without a GPU and exports every entry point that
+include/sk.h declares (no compute calls)."""
+import ctypes
+import subprocess
+
+from paper_1511_00152_gb300 import build as skbuild
+from paper_1511_00152_gb300 import _lib
+
+
+def test_library_builds_and_exports_header_symbols():
+    path = skbuild.build()
+    lib = ctypes.CDLL(path)
+    declared = _lib.header_symbols()
+    assert len(declared) >= 15
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+    # nothing else sk_* is exported that the header does not declare
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True)
+    if out.returncode == 0:
+        exported = {ln.split()[-1] for ln in out.stdout.splitlines() if " T sk_" in ln}
+        assert exported <= set(declared), exported - set(declared)
+
+
+def test_binding_covers_header():
+    lib = _lib.load(skbuild.build())
+    for s in _lib.header_symbols():
+        assert getattr(lib, s).argtypes is not None or s == "sk_last_error", s
+
+
+def test_host_validation_without_gpu():
+    """Argument checks run on the host and need no device."""
+    lib = _lib.load(skbuild.build())
+    h = ctypes.c_void_p(0)
+    assert lib.sk_init(ctypes.byref(h), 0, 1, 0) == _lib.SK_EINVAL
+    assert lib.sk_init(ctypes.byref(h), 9000, 1, 0) == _lib.SK_EUNSUPPORTED
+    assert lib.sk_init(ctypes.byref(h), 1000, 1025, 0) == _lib.SK_EINVAL
+    assert lib.sk_init(ctypes.byref(h), 1000, 50, 7) == _lib.SK_OK
+    assert lib.sk_ptilde(h) == 1024
+    nul = ctypes.c_void_p(0)
+    assert lib.sk_compress(h, nul, 3, 1000, 0, nul, nul, nul) == _lib.SK_EINVAL
+    assert b"NULL" in lib.sk_last_error()
+    assert lib.sk_cov_topk_workspace(1024, 10) > 0
+    assert lib.sk_cov_topk_workspace(1024, 0) == -1
+    lib.sk_destroy(h)
+    lib.sk_destroy(nul)

@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated per result):
+  idx      bit-exact
+  val      |val_gpu - val_oracle| <= 1e-5 * ||x_r||_2       (FP32 transform)
+  Y dense  same bound per row
+  Gram     FP32 scatter: relative Frobenius <= 1e-6
+  C_n      relative Frobenius <= 1e-6 (FP32 Gram)
+  labels   identical where the oracle's best and second-best restricted
+           distances differ by more than 1e-4 relative (near-tie band)
+  sums     cnt and nk exact; S within 1e-5 relative (float products summed in
+           FP32 per CTA then FP64)
+  centres  relative error <= 1e-5
+  top-k    max sin(principal angle) <= 1e-6
+  unmix    |err| <= 1e-5 * ||row||
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_00152_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sk():
+    from paper_1511_00152_gb300 import _lib
+    return _lib
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _check_compress(sk, X, m, seed, row0=0, ldx_pad=0):
+    n, p = X.shape
+    ctx = sk.sk_init(p, m, seed)
+    if ldx_pad:
+        Xw = np.zeros((n, p + ldx_pad), np.float32)
+        Xw[:, :p] = X
+        Xd = _dev(Xw)[:, :p]
+    else:
+        Xd = _dev(X)
+    idx, val = sk.sk_compress(ctx, Xd, row0=row0)
+    torch.cuda.synchronize()
+    oi, ov = oracle.compress(X, m, seed, row0=row0)
+    gi = idx.cpu().numpy()
+    gv = val.cpu().numpy().astype(np.float64)
+    assert np.array_equal(gi, oi), "mask indices differ"
+    norms = np.linalg.norm(X.astype(np.float64), axis=1)
+    err = np.abs(gv - ov).max(axis=1) if m else np.zeros(n)
+    assert np.all(err <= 1e-5 * np.maximum(norms, 1e-30)), float((err / np.maximum(norms, 1e-30)).max())
+    return ctx
+
+
+@pytest.mark.parametrize("p,m,n", [
+    (64, 8, 2000),      # tiny workload shape
+    (50, 7, 333),       # zero padding to 64, ragged row count
+    (1024, 51, 3000),   # K-means workload shape
+    (1000, 50, 1000),   # padding to 1024
+    (4096, 205, 300),   # PCA workload shape
+    (2048, 102, 500),   # streaming workload shape
+    (8192, 820, 40),    # largest pt, m = 10%
+    (256, 13, 1000),
+    (8, 3, 100),
+    (1, 1, 10),
+    (2, 2, 10),
+    (16, 16, 50),       # m = pt: a permutation per row
+    (128, 1, 77),
+    (4, 4, 1),
+    (700, 35, 5),
+])
+def test_compress_parity(sk, p, m, n):
+    X = synth.lowrank_spiky(n, p, seed=p * 7 + n, sv=(10.0, 6.0, 4.0, 2.0, 1.0)[: max(1, min(5, p))])
+    _check_compress(sk, X, m, seed=1234 + p)
+
+
+def test_compress_row0_and_strided(sk):
+    X = synth.mixture(777, 300, 4, seed=3)[0]
+    _check_compress(sk, X, 15, seed=99, row0=(1 << 33) + 17, ldx_pad=13)
+    _check_compress(sk, X, 15, seed=99, row0=5, ldx_pad=4)
+
+
+def test_compress_chunked_equals_single(sk):
+    X = _dev(synth.uniform(5000, 1024, seed=4))
+    ctx = sk.sk_init(1024, 51, 7)
+    i1, v1 = sk.sk_compress(ctx, X)
+    parts = [(0, 1234), (1234, 1235), (1235, 4000), (4000, 5000)]
+    for a, b in parts:
+        ia, va = sk.sk_compress(ctx, X[a:b].contiguous(), row0=a)
+        assert torch.equal(ia, i1[a:b]) and torch.equal(va, v1[a:b])
+
+
+@pytest.mark.parametrize("p", [64, 100, 1024, 4096, 8192])
+def test_precondition_parity(sk, p):
+    X = synth.lowrank_spiky(37, p, seed=p)
+    ctx = sk.sk_init(p, 2, 55)
+    Y = sk.sk_precondition(ctx, _dev(X)).cpu().numpy().astype(np.float64)
+    Yo = oracle.precondition(X, 55)
+    norms = np.linalg.norm(X.astype(np.float64), axis=1)
+    assert np.all(np.abs(Y - Yo).max(axis=1) <= 1e-5 * norms)
+
+
+def _near_tie_mask(idx, val, mu, pt, rel=1e-4):
+    """Rows whose best and second-best oracle distances are within rel."""
+    K = mu.shape[0]
+    n, m = idx.shape
+    d = np.zeros((n, K))
+    for k in range(K):
+        diff = val - mu[k][idx]
+        d[:, k] = (diff * diff).sum(1)
+    ds = np.sort(d, axis=1)
+    if K == 1:
+        return np.zeros(n, bool)
+    return (ds[:, 1] - ds[:, 0]) <= rel * np.maximum(ds[:, 0], 1e-30)
+
+
+@pytest.mark.parametrize("p,m,n,K", [(64, 8, 2000, 5), (1024, 51, 4000, 10), (2048, 102, 1500, 8),
+                                     (256, 5, 3000, 50), (128, 13, 500, 1), (512, 26, 700, 70),
+                                     (64, 8, 300, 200)])
+def test_kmeans_step_teacher_forced(sk, p, m, n, K):
+    """One fused assign+update pass from the oracle's centres (teacher forcing)."""
+    X = synth.mixture(n, p, min(K, 10), seed=p + K)[0]
+    seed = 17
+    ctx = sk.sk_init(p, m, seed)
+    pt = ctx.pt
+    idx, val = sk.sk_compress(ctx, _dev(X))
+    oi, ov = oracle.compress(X, m, seed)
+    rows = synth.init_rows(n, K, seed)
+    mu = oracle.precondition(X[rows], seed)
+    labels_o, dist_o = oracle.kmeans_assign(oi, ov, mu, pt)
+    mu_new_o, counts_o, nk_o = oracle.kmeans_update(oi, ov, labels_o, mu, pt)
+
+    mu_d = _dev(mu.astype(np.float32))
+    # assign alone
+    lab_a, _ = sk.sk_kmeans_assign(ctx, idx, val, mu_d)
+    # fused step
+    S = torch.zeros((K, pt), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros((K, pt), dtype=torch.int32, device="cuda")
+    nk = torch.zeros(K, dtype=torch.int64, device="cuda")
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    dist = torch.empty(n, dtype=torch.float32, device="cuda")
+    sk.sk_kmeans_reset(ctx, S, cnt, nk)
+    sk.sk_kmeans_step(ctx, idx, val, mu_d, labels, S, cnt, nk, dist=dist)
+    torch.cuda.synchronize()
+    gl = labels.cpu().numpy()
+    assert np.array_equal(gl, lab_a.cpu().numpy())
+    tie = _near_tie_mask(oi, ov, mu, pt)
+    assert np.array_equal(gl[~tie], labels_o[~tie])
+    same = gl == labels_o
+    assert np.allclose(dist.cpu().numpy()[same], dist_o[same], rtol=1e-4, atol=1e-6)
+    if np.all(same):
+        assert np.array_equal(cnt.cpu().numpy(), counts_o)
+        assert np.array_equal(nk.cpu().numpy(), nk_o)
+        # S against the oracle's sums: S_kj = mu_new * counts where counts > 0
+        So = np.where(counts_o > 0, mu_new_o * counts_o, 0.0)
+        Sg = S.cpu().numpy()
+        scale = np.abs(So).max() + 1e-30
+        assert np.abs(Sg - So).max() <= 1e-5 * scale
+        sk.sk_kmeans_finalize(ctx, S, cnt, mu_d)
+        mug = mu_d.cpu().numpy().astype(np.float64)
+        assert np.abs(mug - mu_new_o).max() <= 1e-5 * (np.abs(mu_new_o).max() + 1e-30)
+    # update alone under the oracle labels
+    S2 = torch.zeros_like(S)
+    c2 = torch.zeros_like(cnt)
+    n2 = torch.zeros_like(nk)
+    sk.sk_kmeans_update(ctx, idx, val, _dev(labels_o), K, S2, c2, n2)
+    torch.cuda.synchronize()
+    assert np.array_equal(c2.cpu().numpy(), counts_o)
+    assert np.array_equal(n2.cpu().numpy(), nk_o)
+
+
+def test_kmeans_end_to_end_tiny(sk):
+    """Tiny workload: n=2000, p=64, m=8, K=5, 10 iterations, CUDA graph."""
+    from paper_1511_00152_gb300 import pipeline
+    n, p, m, K, seed = 2000, 64, 8, 5, 1
+    X = synth.lowrank_spiky(n, p, seed=seed)
+    ctx = sk.sk_init(p, m, seed)
+    Xd = _dev(X)
+    idx, val = sk.sk_compress(ctx, Xd)
+    rows = synth.init_rows(n, K, seed)
+    mu0 = pipeline.initial_centres(ctx, Xd, rows)
+    st = pipeline.KMeansState(ctx, n, K)
+    labels, mu = st.run(idx, val, mu0, iters=10, use_graph=True)
+    torch.cuda.synchronize()
+    oi, ov = oracle.compress(X, m, seed)
+    lo, muo, hist = oracle.kmeans(oi, ov, oracle.precondition(X[rows], seed), ctx.pt, 10)
+    agree = float(np.mean(labels.cpu().numpy() == lo))
+    assert agree >= 0.99, agree
+    if agree == 1.0:
+        rel = np.linalg.norm(mu.cpu().numpy() - muo) / np.linalg.norm(muo)
+        assert rel <= 1e-5, rel
+    # graph replay reproduces the eager loop
+    st2 = pipeline.KMeansState(ctx, n, K)
+    l2, mu2 = st2.run(idx, val, mu0, iters=10, use_graph=False)
+    assert torch.equal(l2, labels)
+    assert torch.allclose(mu2, mu, rtol=1e-6, atol=1e-7)
+    # un-mixed centres
+    um = sk.sk_unmix(ctx, mu).cpu().numpy().astype(np.float64)
+    umo = oracle.unmix(mu.cpu().numpy().astype(np.float64), p, seed)
+    assert np.abs(um - umo).max() <= 1e-5 * np.abs(umo).max()
+
+
+@pytest.mark.parametrize("p,m,n", [(64, 8, 2000), (1024, 51, 3000), (300, 20, 1000), (4096, 205, 200),
+                                   (256, 2, 500), (128, 128, 100)])
+def test_gram_fp32_and_cov_parity(sk, p, m, n):
+    X = synth.lowrank_spiky(n, p, seed=n + p)
+    seed = 3
+    ctx = sk.sk_init(p, m, seed)
+    pt = ctx.pt
+    idx, val = sk.sk_compress(ctx, _dev(X))
+    oi, ov = oracle.compress(X, m, seed)
+    Go = oracle.gram(oi, ov, pt)
+    G = torch.empty((pt, pt), dtype=torch.float64, device="cuda")
+    sk.sk_cov_reset(ctx, G)
+    # two chunks accumulate into the same G
+    h = n // 3
+    sk.sk_cov_accumulate(ctx, sk.SK_GRAM_FP32, idx[:h].contiguous(), val[:h].contiguous(), G)
+    sk.sk_cov_accumulate(ctx, sk.SK_GRAM_FP32, idx[h:].contiguous(), val[h:].contiguous(), G)
+    C = sk.sk_cov_finalize(ctx, G, n)
+    torch.cuda.synchronize()
+    Gg = np.triu(G.cpu().numpy())
+    Gu = np.triu(Go)
+    assert np.linalg.norm(Gg - Gu) <= 1e-6 * np.linalg.norm(Gu)
+    Co = oracle.cov_finalize(Go, n, m)
+    Cg = C.cpu().numpy()
+    assert np.allclose(Cg, Cg.T)
+    assert np.linalg.norm(Cg - Co) <= 1e-6 * np.linalg.norm(Co)
+
+
+def test_cov_finalize_exact_from_oracle_gram(sk):
+    p, m, n = 256, 20, 50
+    ctx = sk.sk_init(p, m, 1)
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((p, p))
+    Go = A + A.T
+    C = sk.sk_cov_finalize(ctx, _dev(Go), n).cpu().numpy()
+    Co = oracle.cov_finalize(Go, n, m)
+    assert np.abs(C - Co).max() <= 1e-14 * np.abs(Co).max()
+
+
+@pytest.mark.parametrize("pt,k", [(64, 5), (1024, 10), (256, 20)])
+def test_topk_parity(sk, pt, k):
+    """Top-k subspace of a symmetric matrix with a clear spectral gap."""
+    rng = np.random.default_rng(pt + k)
+    Q, _ = np.linalg.qr(rng.standard_normal((pt, pt)))
+    lam = np.concatenate([np.linspace(10, 5, k), rng.uniform(-0.5, 1.0, pt - k)])
+    C = (Q * lam) @ Q.T
+    C = 0.5 * (C + C.T)
+    ctx = sk.sk_init(pt, 2, 8)
+    ev, U = sk.sk_cov_topk(ctx, _dev(C), k, iters=60)
+    torch.cuda.synchronize()
+    wo, Vo = oracle.pca_topk(C, k)
+    assert np.allclose(ev.cpu().numpy(), wo, rtol=1e-9, atol=1e-9)
+    Ug = U.cpu().numpy().T
+    s = np.linalg.svd(Vo.T @ Ug, compute_uv=False)
+    sin_max = np.sqrt(max(0.0, 1.0 - s.min() ** 2))
+    assert sin_max <= 1e-6, sin_max
+
+
+def test_pca_tiny_workload(sk):
+    """Tiny workload: C_n from n=2000, p=64, m=8 and its top-5 subspace."""
+    from paper_1511_00152_gb300 import pipeline
+    n, p, m, seed = 2000, 64, 8, 1
+    X = synth.lowrank_spiky(n, p, seed=seed)
+    ctx = sk.sk_init(p, m, seed)
+    idx, val = sk.sk_compress(ctx, _dev(X))
+    C = pipeline.covariance(ctx, idx, val, sk.SK_GRAM_FP32)
+    ev, Up, U = pipeline.pca(ctx, C, 5, iters=200)
+    torch.cuda.synchronize()
+    oi, ov = oracle.compress(X, m, seed)
+    Co = oracle.cov(oi, ov, ctx.pt)
+    wo, Vo = oracle.pca_topk(Co, 5)
+    assert np.allclose(ev.cpu().numpy(), wo, rtol=1e-5)
+    s = np.linalg.svd(Vo.T @ Up.cpu().numpy().T, compute_uv=False)
+    assert np.sqrt(max(0.0, 1 - s.min() ** 2)) <= 1e-4
+    Uo = oracle.unmix(Vo.T.copy(), p, seed)
+    s2 = np.linalg.svd(Uo @ U.cpu().numpy().T, compute_uv=False)
+    assert np.sqrt(max(0.0, 1 - s2.min() ** 2)) <= 1e-4
+
+
+def test_unmix_parity(sk):
+    p = 1000
+    ctx = sk.sk_init(p, 10, 21)
+    M = np.random.default_rng(1).standard_normal((7, ctx.pt))
+    out = sk.sk_unmix(ctx, _dev(M.astype(np.float32))).cpu().numpy().astype(np.float64)
+    ref = oracle.unmix(M.astype(np.float32).astype(np.float64), p, 21)
+    assert np.abs(out - ref).max() <= 1e-5 * np.linalg.norm(M, axis=1).max()
+    out64 = sk.sk_unmix(ctx, _dev(M)).cpu().numpy()
+    assert np.abs(out64 - oracle.unmix(M, p, 21)).max() <= 1e-12 * np.abs(M).max()
+
+
+def test_invalid_arguments_rejected_before_launch(sk):
+    import ctypes
+    lib = sk.load()
+    h = ctypes.c_void_p(0)
+    assert lib.sk_init(ctypes.byref(h), 0, 1, 0) == sk.SK_EINVAL
+    assert lib.sk_init(ctypes.byref(h), 10000, 1, 0) == sk.SK_EUNSUPPORTED
+    assert lib.sk_init(ctypes.byref(h), 64, 65, 0) == sk.SK_EINVAL
+    assert lib.sk_init(ctypes.byref(h), 64, 0, 0) == sk.SK_EINVAL
+    ctx = sk.sk_init(64, 1, 0)
+    nul = ctypes.c_void_p(0)
+    assert lib.sk_compress(ctx.handle, nul, 10, 64, 0, nul, nul, nul) == sk.SK_EINVAL
+    assert lib.sk_compress(ctx.handle, nul, -1, 64, 0, nul, nul, nul) == sk.SK_EINVAL
+    assert lib.sk_compress(ctx.handle, nul, 0, 64, 0, nul, nul, nul) == sk.SK_OK  # n = 0 no-op
+    assert lib.sk_compress(ctx.handle, nul, 5, 10, 0, nul, nul, nul) == sk.SK_EINVAL  # ldx < p
+    G = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    # m = 1: covariance needs m >= 2 (Thm. B1)
+    assert lib.sk_cov_finalize(ctx.handle, sk._ptr(G), 10, sk._ptr(G), nul) == sk.SK_EINVAL
+    ctx2 = sk.sk_init(64, 4, 0)
+    assert lib.sk_cov_finalize(ctx2.handle, sk._ptr(G), 10, sk._ptr(G), nul) == sk.SK_EINVAL  # overlap
+    assert lib.sk_cov_accumulate(ctx2.handle, 7, nul, nul, 5, nul, nul) == sk.SK_EINVAL
+    assert lib.sk_kmeans_assign(ctx2.handle, nul, nul, 5, nul, 0, nul, nul, nul) == sk.SK_EINVAL
+    assert lib.sk_cov_topk(ctx2.handle, sk._ptr(G), 0, 10, nul, nul, nul, nul) == sk.SK_EINVAL
+    assert "must be" in sk.sk_last_error() or sk.sk_last_error() != ""
+    assert sk.sk_device_status() == sk.SK_OK
