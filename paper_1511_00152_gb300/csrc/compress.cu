@@ -36,7 +36,79 @@ struct CompressParams {
     float *Y;
     float scale;
     int vec;
+    unsigned int *err;  // device error word (bounded waits)
 };
+
+constexpr int kNB = 2;  // staging buffers per warp (one unit in flight ahead)
+constexpr long long kWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    const long long deadline = clock64() + kWaitCycles;
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() > deadline) return false;
+    }
+}
+
+// Stage the raw samples of one unit into buf with 1D bulk copies (TMA),
+// completing on bar.  Lane 0 sets the expected byte count first.
+template <int L>
+__device__ __forceinline__ void issue_unit(const CompressParams &P, int64_t u, int wg, float *buf,
+                                           uint32_t bar, int lane) {
+    constexpr int PT = 1 << L;
+    constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
+    int64_t r0 = u * RPU;
+    int rows = (int)((P.n - r0) < RPU ? (P.n - r0) : RPU);
+    int cols, c0;
+    if constexpr (L <= 10) {
+        c0 = 0;
+        cols = (int)P.p;
+    } else {
+        c0 = 1024 * wg;
+        cols = (int)(P.p - c0 < 1024 ? P.p - c0 : 1024);
+        if (cols < 0) cols = 0;
+    }
+    const uint32_t bytes_row = (uint32_t)cols * 4u;
+    const bool contiguous = (L <= 10) && P.ldx == PT && P.p == PT;
+    const uint32_t total = (uint32_t)rows * bytes_row;
+    if (lane == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
+                     : "memory");
+    }
+    __syncwarp();
+    if (total == 0) return;
+    if (contiguous) {
+        if (lane == 0) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(buf)),
+                "l"(P.X + r0 * P.ldx), "r"(total), "r"(bar)
+                : "memory");
+        }
+    } else {
+        for (int b = lane; b < rows; b += 32) {
+            const float *src = P.X + (r0 + b) * P.ldx + c0;
+            float *dst = buf + ((L <= 10) ? b * PT : 0);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(dst)),
+                "l"(src), "r"(bytes_row), "r"(bar)
+                : "memory");
+        }
+    }
+}
 
 // Swizzled shared-memory slot of unit element e: XOR of bits 2..4 with bits
 // 7..9 makes both the float4 (phase A) and the stride-4 (phase B) access
@@ -131,19 +203,24 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
     }
 }
 
-template <int L, bool DENSE>
+template <int L, bool DENSE, bool TMA>
 __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams P) {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;  // warps per row group
     constexpr int NG = kWarps / G;                // row groups per CTA
     constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
     constexpr int BUF = (L <= 10) ? 1024 : PT;
+    constexpr int NBUF = TMA ? kNB : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = warp / G, wg = warp % G;
-    float *ybuf = reinterpret_cast<float *>(smem_raw) + grp * BUF;
-    uint32_t *A = reinterpret_cast<uint32_t *>(smem_raw + NG * BUF * 4) + grp * PT;
-    uint32_t *hit = reinterpret_cast<uint32_t *>(smem_raw + NG * BUF * 4 + NG * PT * 4) + grp * 32;
+    float *ybufs = reinterpret_cast<float *>(smem_raw) + grp * NBUF * BUF;
+    float *ybuf = ybufs;
+    unsigned char *after = smem_raw + (size_t)NG * NBUF * BUF * 4;
+    uint32_t *A = reinterpret_cast<uint32_t *>(after) + grp * PT;
+    uint32_t *hit = reinterpret_cast<uint32_t *>(after + (size_t)NG * PT * 4) + grp * 32;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(after + (size_t)NG * PT * 4 + NG * 32 * 4) +
+                     warp * kNB;
 
     if constexpr (!DENSE) {
         if (wg == 0)
@@ -162,9 +239,56 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
 
     const int64_t nunits = (L <= 10) ? (P.n + RPU - 1) / RPU : P.n;
     const int64_t stride = (int64_t)gridDim.x * NG;
-    for (int64_t u = (int64_t)blockIdx.x * NG + grp; u < nunits; u += stride) {
+    const int64_t u_first = (int64_t)blockIdx.x * NG + grp;
+    if constexpr (TMA) {
+        if (lane == 0)
+            for (int b = 0; b < kNB; ++b)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        __syncwarp();
+        if (u_first < nunits)
+            issue_unit<L>(P, u_first, wg, ybufs + ((L > 10) ? 1024 * wg : 0), smem_u32(mbar), lane);
+    }
+    int64_t kloc = 0;  // units processed by this group
+    for (int64_t u = u_first; u < nunits; u += stride, ++kloc) {
         const int64_t r0 = u * RPU;
         float v[32];
+        if constexpr (TMA) {
+            const int bsel = (int)(kloc & 1);
+            ybuf = ybufs + bsel * BUF;
+            // the other buffer's last reader (previous unit's gathers) is done
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            group_sync<G>(grp);
+            if (u + stride < nunits)
+                issue_unit<L>(P, u + stride, wg, ybufs + (bsel ^ 1) * BUF + ((L > 10) ? 1024 * wg : 0),
+                              smem_u32(mbar + (bsel ^ 1)), lane);
+            if (!mbar_wait_bounded(smem_u32(mbar + bsel), (uint32_t)((kloc >> 1) & 1))) {
+                if (lane == 0 && P.err) atomicOr(P.err, 2u);
+                // wait (bounded) for the copy still in flight, then stop
+                mbar_wait_bounded(smem_u32(mbar + (bsel ^ 1)), (uint32_t)(((kloc + 1) >> 1) & 1));
+                break;
+            }
+            float *wb = ybuf + ((L > 10) ? 1024 * wg : 0);
+            // zero what the copies did not fill: padding columns and rows past n
+            const bool ragged = (L <= 10) ? (r0 + RPU > P.n) : false;
+            const int cend = (L <= 10) ? (int)P.p : (int)(P.p - 1024 * wg);
+            if (ragged || cend < ((L <= 10) ? PT : 1024)) {
+                for (int e = lane; e < 1024; e += 32) {
+                    const int b = (L <= 10) ? (e >> L) : 0;
+                    const int c = (L <= 10) ? (e & (PT - 1)) : e;
+                    if (r0 + b >= P.n || c >= cend) wb[e] = 0.f;
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int ip = 0; ip < 8; ++ip) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(wb + 128 * ip + 4 * lane);
+                v[4 * ip + 0] = x4.x;
+                v[4 * ip + 1] = x4.y;
+                v[4 * ip + 2] = x4.z;
+                v[4 * ip + 3] = x4.w;
+            }
+        } else {
         // ---- load (phase A layout): element e = 128*ip + 4*lane + q
 #pragma unroll
         for (int ip = 0; ip < 8; ++ip) {
@@ -199,6 +323,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
                 }
             }
         }
+        }
         // ---- D: flip the sign bit where D_j = -1
 #pragma unroll
         for (int r = 0; r < 32; ++r)
@@ -218,7 +343,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
                 }
             }
         }
-        group_sync<G>(grp);  // previous unit's gathers are done with ybuf
+        // every lane has read its samples (TMA) / previous gathers are done
+        group_sync<G>(grp);
         float *wbuf = ybuf + ((L > 10) ? 1024 * wg : 0);
 #pragma unroll
         for (int ip = 0; ip < 8; ++ip) {
@@ -310,22 +436,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
     }
 }
 
-template <int L, bool DENSE>
-cudaError_t launch_L(const CompressParams &P, cudaStream_t s) {
+template <int L, bool DENSE, bool TMA>
+cudaError_t launch_LT(const CompressParams &P, cudaStream_t s) {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;
     constexpr int NG = kWarps / G;
     constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
     constexpr int BUF = (L <= 10) ? 1024 : PT;
-    const size_t smem = (size_t)NG * BUF * 4 + (DENSE ? 0 : (size_t)NG * PT * 4 + NG * 32 * 4);
-    auto kern = compress_kernel<L, DENSE>;
-    static bool configured = false;  // per instantiation; attribute is per device context
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    constexpr int NBUF = TMA ? kNB : 1;
+    const size_t smem = (size_t)NG * NBUF * BUF * 4 + (size_t)NG * PT * 4 + NG * 32 * 4 +
+                        (size_t)kWarps * kNB * 8;
+    auto kern = compress_kernel<L, DENSE, TMA>;
+    cudaError_t e0 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (e0 != cudaSuccess) return e0;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -338,6 +462,15 @@ cudaError_t launch_L(const CompressParams &P, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, kWarps * 32, smem, s>>>(P);
     return cudaGetLastError();
+}
+
+template <int L, bool DENSE>
+cudaError_t launch_L(const CompressParams &P, cudaStream_t s) {
+    // bulk copies need 16-byte aligned rows whose byte length is a multiple of 16
+    if constexpr (L >= 2) {
+        if (P.vec) return launch_LT<L, DENSE, true>(P, s);
+    }
+    return launch_LT<L, DENSE, false>(P, s);
 }
 
 template <bool DENSE>
@@ -380,6 +513,7 @@ cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t 
     P.Y = Y;
     P.scale = (float)(1.0 / sqrt((double)c.pt));
     P.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (c.p % 4 == 0) && (ldx % 4 == 0);
+    P.err = device_error_word();
     if (n == 0) return cudaSuccess;
     return Y ? dispatch<true>(c.log2pt, P, s) : dispatch<false>(c.log2pt, P, s);
 }

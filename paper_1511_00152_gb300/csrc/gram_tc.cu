@@ -27,6 +27,14 @@ namespace sk {
 
 __device__ unsigned int g_device_error = 0u;
 
+unsigned int *device_error_word() {
+    // device address of g_device_error for kernels in other translation units
+    // (looked up on every call: cheap, and correct for whichever device is current)
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_device_error) != cudaSuccess) return nullptr;
+    return static_cast<unsigned int *>(ptr);
+}
+
 cudaError_t take_device_error(unsigned int *flag) {
     unsigned int zero = 0;
     cudaError_t e = cudaMemcpyFromSymbol(flag, g_device_error, sizeof(*flag));
@@ -43,6 +51,7 @@ constexpr int kThreads = kProducers + 32;  // + the MMA warp
 constexpr int kSlab = 64;                  // rows per K-slab (128 bytes of BF16)
 constexpr int kTileM = 128;
 constexpr int kSegmentRows = 65536;
+constexpr int kChunk = 16;                 // entries per producer thread per chunk
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcParams {
@@ -230,44 +239,81 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
         __syncwarp();
     } else {
         // ---------------- producers (then epilogue)
+        // The entries of slab i are the contiguous ELL range [r0*m, r0*m + rows*m).
+        // They are consumed in chunks of kChunk entries per thread; the loads
+        // of the next chunk are issued before the current chunk is scattered,
+        // so the L2 latency overlaps the scatter, the stage wait and the zeroing.
         const int ptid = tid;  // 0 .. kProducers-1
         const int m = P.m;
-        bool ok = true;
-        for (int64_t i = 0; i < nslabs && ok; ++i) {
-            const int s = (int)(i % S);
-            const uint32_t u = (uint32_t)(i / S);
-            if (u > 0) {
-                if (!mbar_wait(smem_u32(bars + S + s), (u - 1) & 1u, deadline, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(&g_device_error, 1u);
-                    ok = false;
+        const float inv_m = 1.0f / (float)m;
+        const int per_chunk = kProducers * kChunk;
+        int64_t slab = 0;      // slab of the chunk held in registers
+        int pass = 0;          // chunk index within that slab
+        int cj[kChunk], nj[kChunk];
+        float cv[kChunk], nv[kChunk];
+        auto slab_total = [&](int64_t i) -> int {
+            const int64_t r0 = r_begin + i * kSlab;
+            const int64_t rows = (r_end - r0) < kSlab ? (r_end - r0) : kSlab;
+            return (int)rows * m;
+        };
+        auto load_chunk = [&](int64_t i, int ps, int *jj, float *vv) {
+            const int total = slab_total(i);
+            const int64_t ebase = (r_begin + i * kSlab) * (int64_t)m;
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int e = ps * per_chunk + q * kProducers + ptid;
+                if (e < total) {
+                    jj[q] = __ldg(P.idx + ebase + e);
+                    vv[q] = __ldg(P.val + ebase + e);
+                } else {
+                    jj[q] = -1;
+                    vv[q] = 0.f;
                 }
             }
-            // all producers agree on ok before touching the stage
-            named_sync(1, kProducers);
-            if (*abort_flag) {
-                ok = false;
-                break;
-            }
+        };
+        if (nslabs > 0) load_chunk(0, 0, cj, cv);
+        bool ok = true;
+        while (slab < nslabs && ok) {
+            const int s = (int)(slab % S);
+            const uint32_t u = (uint32_t)(slab / S);
+            const int total = slab_total(slab);
+            const int npass = (total + per_chunk - 1) / per_chunk;
             unsigned char *st = tiles + (size_t)s * P.stage_bytes;
-            const int zero_bytes = P.stage_bytes;
-            for (int off = ptid * 16; off < zero_bytes; off += kProducers * 16)
-                *reinterpret_cast<uint4 *>(st + off) = make_uint4(0u, 0u, 0u, 0u);
-            named_sync(1, kProducers);
+            if (pass == 0) {
+                if (u > 0) {
+                    if (!mbar_wait(smem_u32(bars + S + s), (u - 1) & 1u, deadline, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(&g_device_error, 1u);
+                    }
+                }
+                named_sync(1, kProducers);  // every producer sees the same abort state
+                if (*abort_flag) {
+                    ok = false;
+                    break;
+                }
+                for (int off = ptid * 16; off < P.stage_bytes; off += kProducers * 16)
+                    *reinterpret_cast<uint4 *>(st + off) = make_uint4(0u, 0u, 0u, 0u);
+                named_sync(1, kProducers);
+            }
+            // prefetch the next chunk (this slab's next pass, or the next slab's first)
+            const bool last_pass = pass + 1 >= npass;
+            const int64_t nslab = last_pass ? slab + 1 : slab;
+            const int npass_next = last_pass ? 0 : pass + 1;
+            if (nslab < nslabs) load_chunk(nslab, npass_next, nj, nv);
             unsigned char *A_hi = st, *B_hi = st + a_bytes;
             unsigned char *A_lo = st + a_bytes + b_bytes, *B_lo = A_lo + a_bytes;
-            const int64_t r0 = r_begin + i * kSlab;
-            const int rows_here = (int)((r_end - r0) < kSlab ? (r_end - r0) : kSlab);
-            const int64_t ebase = r0 * (int64_t)m;
-            const int total = rows_here * m;
-            for (int e = ptid; e < total; e += kProducers) {
-                const int j = __ldg(P.idx + ebase + e);
-                const float v = __ldg(P.val + ebase + e);
-                const int k = e / m;  // row within the slab = K index
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int j = cj[q];
                 const int a = j - I0, b = j - J0;
                 const bool inA = (unsigned)a < (unsigned)kTileM;
                 const bool inB = (unsigned)b < (unsigned)N;
                 if (inA || inB) {
+                    const int e = pass * per_chunk + q * kProducers + ptid;
+                    // row within the slab: exact since e + 0.5 is at least 0.5 away
+                    // from every multiple of m and e < 2^20
+                    const int k = (int)(((float)e + 0.5f) * inv_m);
+                    const float v = cv[q];
                     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
                     if (inA) *reinterpret_cast<__nv_bfloat16 *>(A_hi + sw_off(a, k)) = hi;
                     if (inB) *reinterpret_cast<__nv_bfloat16 *>(B_hi + sw_off(b, k)) = hi;
@@ -278,10 +324,21 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
                     }
                 }
             }
-            // generic-proxy writes -> visible to the tensor core (async proxy)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            named_sync(1, kProducers);
-            if (ptid == 0) mbar_arrive(smem_u32(bars + s));
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                cj[q] = nj[q];
+                cv[q] = nv[q];
+            }
+            if (last_pass) {
+                // generic-proxy writes -> visible to the tensor core (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                named_sync(1, kProducers);
+                if (ptid == 0) mbar_arrive(smem_u32(bars + s));
+                ++slab;
+                pass = 0;
+            } else {
+                ++pass;
+            }
         }
         // ---------------- epilogue: TMEM -> FP64 Gram
         const bool have = nslabs > 0;

@@ -19,7 +19,8 @@ namespace sk {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 1024;
+constexpr int kThreads = 512;
+constexpr int kWarpsK = kThreads / 32;
 
 struct KmParams {
     const int32_t *idx;
@@ -28,6 +29,7 @@ struct KmParams {
     int m;
     int pt;
     int K, Kpad, LPR, RW;
+    int stage_cap;  // staged (idx, val) entries per warp
     const float *mu;
     int32_t *labels;
     float *dist;
@@ -37,14 +39,33 @@ struct KmParams {
     int do_assign, do_update;
 };
 
-template <int KPL, bool MU_SMEM, bool PRIV>
+// Packed FP32 pairs (two independent IEEE round-to-nearest operations).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sqacc2(uint64_t d, uint64_t acc) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
+    return r;
+}
+
+template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE>
 __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
+    constexpr int NP = KPL / 2;  // packed pairs per lane
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *mus = reinterpret_cast<float *>(smem_raw);
-    const size_t mu_bytes = (MU_SMEM && P.do_assign) ? (size_t)P.pt * P.Kpad * 4 : 0;
-    float *sS = reinterpret_cast<float *>(smem_raw + mu_bytes);
-    int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + mu_bytes + (PRIV ? (size_t)P.K * P.pt * 4 : 0));
-    int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + mu_bytes + (PRIV ? (size_t)P.K * P.pt * 8 : 0));
+    size_t off = 0;
+    float *mus = reinterpret_cast<float *>(smem_raw + off);
+    if (MU_SMEM && P.do_assign) off += (size_t)P.pt * P.Kpad * 4;
+    float *sS = reinterpret_cast<float *>(smem_raw + off);
+    int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
+    int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
+    if (PRIV && P.do_update) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
+    int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + off);
 
     const int tid = threadIdx.x;
     const int KP = P.K * P.pt;
@@ -63,63 +84,85 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     }
     __syncthreads();
 
-    const int lane = tid & 31;
-    const int sub = lane / P.LPR;            // row slot of this lane in the warp
-    const int kl = lane - sub * P.LPR;       // centre group of this lane
+    const int lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / P.LPR;       // row slot of this lane in the warp
+    const int kl = lane - sub * P.LPR;  // centre group of this lane
     const int kbase = kl * KPL;
     const bool lane_used = sub < P.RW;
+    int2 *stage = stage_all + (size_t)warp * P.stage_cap;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int m = P.m;
+    const int pmask = P.pt - 1;
 
     for (int64_t base = gwarp * P.RW; base < P.n; base += nwarps * P.RW) {
+        const int rows_here = (int)((P.n - base) < P.RW ? (P.n - base) : P.RW);
+        if constexpr (STAGE) {
+            // this pass's rows are contiguous in the ELL arrays: coalesced copy
+            const int total = rows_here * m;
+            const int32_t *gi = P.idx + base * m;
+            const float *gv = P.val + base * m;
+            for (int e = lane; e < total; e += 32)
+                stage[e] = make_int2(__ldg(gi + e), __float_as_int(__ldg(gv + e)));
+            __syncwarp();
+        }
         const int64_t i = base + sub;
-        const bool row_ok = lane_used && i < P.n;
+        const bool row_ok = lane_used && sub < rows_here;
         int label = 0;
         if (P.do_assign) {
-            float acc[KPL];
+            uint64_t acc[NP];
 #pragma unroll
-            for (int q = 0; q < KPL; ++q) acc[q] = 0.f;
+            for (int q = 0; q < NP; ++q) acc[q] = 0ull;
             if (row_ok) {
+                const int2 *rs = stage + sub * m;
                 const int32_t *ri = P.idx + i * m;
                 const float *rv = P.val + i * m;
 #pragma unroll 4
                 for (int t = 0; t < m; ++t) {
-                    // indices outside [0, pt) (not produced by sk_compress) wrap
-                    const int j = __ldg(ri + t) & (P.pt - 1);
-                    const float v = __ldg(rv + t);
+                    int j;
+                    float v;
+                    if constexpr (STAGE) {
+                        const int2 iv = rs[t];
+                        j = iv.x & pmask;  // indices outside [0, pt) wrap
+                        v = __int_as_float(iv.y);
+                    } else {
+                        j = __ldg(ri + t) & pmask;
+                        v = __ldg(rv + t);
+                    }
+                    const uint64_t vv = pack2(v, v);
                     if constexpr (MU_SMEM) {
-                        const float *c = mus + j * P.Kpad + kbase;
+                        const uint64_t *c = reinterpret_cast<const uint64_t *>(mus + j * P.Kpad + kbase);
 #pragma unroll
-                        for (int q = 0; q < KPL; q += 2) {
-                            const float2 c2 = *reinterpret_cast<const float2 *>(c + q);
-                            const float d0 = v - c2.x, d1 = v - c2.y;
-                            acc[q] = fmaf(d0, d0, acc[q]);
-                            acc[q + 1] = fmaf(d1, d1, acc[q + 1]);
-                        }
+                        for (int q = 0; q < NP; ++q) acc[q] = sqacc2(sub2(vv, c[q]), acc[q]);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < KPL; ++q) {
-                            const int k = kbase + q;
-                            const float c = (k < P.K) ? __ldg(P.mu + (int64_t)k * P.pt + j) : 0.f;
-                            const float d = v - c;
-                            acc[q] = fmaf(d, d, acc[q]);
+                        for (int q = 0; q < NP; ++q) {
+                            const int k0 = kbase + 2 * q;
+                            const float c0 = (k0 < P.K) ? __ldg(P.mu + (int64_t)k0 * P.pt + j) : 0.f;
+                            const float c1 = (k0 + 1 < P.K) ? __ldg(P.mu + (int64_t)(k0 + 1) * P.pt + j) : 0.f;
+                            acc[q] = sqacc2(sub2(vv, pack2(c0, c1)), acc[q]);
                         }
                     }
                 }
             }
-            // local argmin over this lane's centres (ascending k: strict < keeps the first)
+            // local argmin over this lane's centres (ascending k, strict <)
             float bd = INFINITY;
             int bk = 0x7fffffff;
 #pragma unroll
-            for (int q = 0; q < KPL; ++q) {
-                const int k = kbase + q;
-                if (k < P.K && acc[q] < bd) {
-                    bd = acc[q];
-                    bk = k;
+            for (int q = 0; q < NP; ++q) {
+                const float d0 = __uint_as_float((uint32_t)acc[q]);
+                const float d1 = __uint_as_float((uint32_t)(acc[q] >> 32));
+                const int k0 = kbase + 2 * q;
+                if (k0 < P.K && d0 < bd) {
+                    bd = d0;
+                    bk = k0;
+                }
+                if (k0 + 1 < P.K && d1 < bd) {
+                    bd = d1;
+                    bk = k0 + 1;
                 }
             }
-            // argmin across the LPR lanes of the row: the row's first lane gathers
+            // argmin across the LPR lanes of the row (ties to the smaller k)
             const int lead = sub * P.LPR;
             for (int o = 1; o < P.LPR; ++o) {
                 const int srcl = (lead + o < 32) ? lead + o : lane;
@@ -140,8 +183,6 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             }
         }
         if (P.do_update) {
-            // labels of this warp's RW rows: slot sub's label lives in lane sub*LPR
-            const int rows_here = (int)((P.n - base) < P.RW ? (P.n - base) : P.RW);
             for (int rs = 0; rs < rows_here; ++rs) {
                 int lab;
                 if (P.do_assign) {
@@ -151,11 +192,17 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                 }
                 if ((unsigned)lab >= (unsigned)P.K) continue;  // invalid caller label: skipped
                 const int64_t ii = base + rs;
-                const int32_t *ri = P.idx + ii * m;
-                const float *rv = P.val + ii * m;
                 for (int t = lane; t < m; t += 32) {
-                    const int j = __ldg(ri + t) & (P.pt - 1);
-                    const float v = __ldg(rv + t);
+                    int j;
+                    float v;
+                    if constexpr (STAGE) {
+                        const int2 iv = stage[rs * m + t];
+                        j = iv.x & pmask;
+                        v = __int_as_float(iv.y);
+                    } else {
+                        j = __ldg(P.idx + ii * m + t) & pmask;
+                        v = __ldg(P.val + ii * m + t);
+                    }
                     const int64_t slot = (int64_t)lab * P.pt + j;
                     if constexpr (PRIV) {
                         atomicAdd(sS + slot, v);
@@ -174,6 +221,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                 }
             }
         }
+        if constexpr (STAGE) __syncwarp();  // stage is rewritten by the next pass
     }
     if (PRIV && P.do_update) {
         __syncthreads();
@@ -199,21 +247,34 @@ __global__ void kmeans_finalize_kernel(int64_t KP, const double *S, const int32_
     }
 }
 
-template <int KPL, bool MU_SMEM, bool PRIV>
+template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE>
 cudaError_t launch_variant(const KmParams &P, size_t smem, cudaStream_t s) {
-    auto kern = kmeans_kernel<KPL, MU_SMEM, PRIV>;
+    auto kern = kmeans_kernel<KPL, MU_SMEM, PRIV, STAGE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
     const int64_t warps_needed = (P.n + P.RW - 1) / P.RW;
-    int64_t blocks = (warps_needed + 31) / 32;
-    if (blocks > sms) blocks = sms;
+    int64_t blocks = (warps_needed + kWarpsK - 1) / kWarpsK;
+    if (blocks > (int64_t)sms * per_sm) blocks = (int64_t)sms * per_sm;
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, kThreads, smem, s>>>(P);
     return cudaGetLastError();
+}
+
+template <int KPL, bool MU_SMEM, bool PRIV>
+cudaError_t launch_stage(KmParams &P, size_t fixed, size_t budget, cudaStream_t s) {
+    const size_t stage_b = (size_t)kWarpsK * P.RW * P.m * 8;
+    if (fixed + stage_b <= budget) {
+        P.stage_cap = P.RW * P.m;
+        return launch_variant<KPL, MU_SMEM, PRIV, true>(P, fixed + stage_b, s);
+    }
+    P.stage_cap = 0;
+    return launch_variant<KPL, MU_SMEM, PRIV, false>(P, fixed, s);
 }
 
 template <int KPL>
@@ -225,12 +286,13 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t mu_b = P.do_assign ? (size_t)P.pt * P.Kpad * 4 : 0;
-    const size_t priv_b = P.do_update ? (size_t)P.K * P.pt * 8 + (size_t)P.K * 4 : 0;
+    const size_t priv_b =
+        P.do_update ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
     const size_t budget = (size_t)smem_max;
-    if (mu_b + priv_b <= budget) return launch_variant<KPL, true, true>(P, mu_b + priv_b, s);
-    if (mu_b <= budget) return launch_variant<KPL, true, false>(P, mu_b, s);
-    if (priv_b <= budget) return launch_variant<KPL, false, true>(P, priv_b, s);
-    return launch_variant<KPL, false, false>(P, 0, s);
+    if (mu_b + priv_b <= budget) return launch_stage<KPL, true, true>(P, mu_b + priv_b, budget, s);
+    if (mu_b <= budget) return launch_stage<KPL, true, false>(P, mu_b, budget, s);
+    if (priv_b <= budget) return launch_stage<KPL, false, true>(P, priv_b, budget, s);
+    return launch_stage<KPL, false, false>(P, 0, budget, s);
 }
 
 }  // namespace

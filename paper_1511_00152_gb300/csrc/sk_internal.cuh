@@ -99,4 +99,6 @@ int64_t topk_workspace(int64_t pt, int k);
 // Reads and clears the device error word of the kernels with bounded waits
 // (bit 0: an mbarrier wait ran out).  Returns cudaSuccess or the copy error.
 cudaError_t take_device_error(unsigned int *flag);
+// Device address of the error word (NULL if it cannot be resolved).
+unsigned int *device_error_word();
 }  // namespace sk

@@ -52,27 +52,32 @@ __global__ void init_v_kernel(double *V, int64_t pt, int b, uint32_t k0, uint32_
     }
 }
 
-// W[c*pt + i] = sum_j C[i*pt + j] * V[c*pt + j] for c < b.  CTA: 64 rows i.
+// W[c*pt + i] += sum_{j in this CTA's range} C[i*pt + j] * V[c*pt + j] for c < b.
+// CTA: 64 rows i (blockIdx.x) times one j-range (blockIdx.y); W must be zeroed
+// before the launch and receives the partial sums with double atomics.
 __global__ void __launch_bounds__(256) panel_kernel(const double *C, const double *V,
-                                                    int64_t pt, int b, double *W) {
+                                                    int64_t pt, int b, int64_t jlen, double *W) {
     __shared__ double Cs[64][33];
     __shared__ double Vs[kMaxB][33];
     const int tid = threadIdx.x;
     const int ri = tid & 63, cg = tid >> 6;  // 4 column groups
     const int64_t i0 = (int64_t)blockIdx.x * 64;
+    const int64_t jb = (int64_t)blockIdx.y * jlen;
+    int64_t je = jb + jlen;
+    if (je > pt) je = pt;
     double acc[kMaxB / 4];
 #pragma unroll
     for (int q = 0; q < kMaxB / 4; ++q) acc[q] = 0.0;
-    for (int64_t j0 = 0; j0 < pt; j0 += 32) {
+    for (int64_t j0 = jb; j0 < je; j0 += 32) {
         for (int e = tid; e < 64 * 32; e += 256) {
             const int r = e >> 5, cc = e & 31;
             const int64_t gi = i0 + r, gj = j0 + cc;
-            Cs[r][cc] = (gi < pt && gj < pt) ? C[gi * pt + gj] : 0.0;
+            Cs[r][cc] = (gi < pt && gj < je) ? C[gi * pt + gj] : 0.0;
         }
         for (int e = tid; e < b * 32; e += 256) {
             const int c = e >> 5, cc = e & 31;
             const int64_t gj = j0 + cc;
-            Vs[c][cc] = (gj < pt) ? V[(int64_t)c * pt + gj] : 0.0;
+            Vs[c][cc] = (gj < je) ? V[(int64_t)c * pt + gj] : 0.0;
         }
         __syncthreads();
 #pragma unroll 4
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(256) panel_kernel(const double *C, const doubl
 #pragma unroll
         for (int q = 0; q < kMaxB / 4; ++q) {
             const int c = cg + 4 * q;
-            if (c < b) W[(int64_t)c * pt + gi] = acc[q];
+            if (c < b) atomicAdd(W + (int64_t)c * pt + gi, acc[q]);
         }
     }
 }
@@ -170,72 +175,97 @@ __global__ void apply_rinv_kernel(const double *W, const double *Rinv, int64_t p
     }
 }
 
-// Cyclic Jacobi eigen-decomposition of the symmetric b x b H (one CTA):
-// H = Q diag(lam) Q^T.
-__global__ void jacobi_kernel(const double *Hin, int b, double *Q, double *lam) {
+// Jacobi eigen-decomposition of the symmetric b x b H (one CTA):
+// H = Q diag(lam) Q^T.  Parallel (round-robin) ordering: each step applies
+// bp/2 disjoint plane rotations at once (bp = b rounded up to even, the extra
+// index is a decoupled zero row/column), bp - 1 steps per sweep, sweeps until
+// the off-diagonal mass is below 1e-30 of the total.
+__global__ void __launch_bounds__(256) jacobi_kernel(const double *Hin, int b, double *Q,
+                                                     double *lam) {
     __shared__ double A[kMaxB][kMaxB + 1];
-    __shared__ double cs[2];
+    __shared__ double rc[kMaxB / 2], rs[kMaxB / 2];
+    __shared__ int rp[kMaxB / 2], rq[kMaxB / 2];
     __shared__ int done;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        const int r = e / b, c = e % b;
-        A[r][c] = 0.5 * (Hin[r * b + c] + Hin[c * b + r]);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int bp = (b + 1) & ~1;
+    const int half = bp / 2;
+    for (int e = tid; e < bp * bp; e += nt) {
+        const int r = e / bp, c = e % bp;
+        A[r][c] = (r < b && c < b) ? 0.5 * (Hin[r * b + c] + Hin[c * b + r]) : 0.0;
     }
-    // Q (global) accumulates the rotations; thread r owns row r of Q.
-    for (int r = tid; r < b; r += blockDim.x)
-        for (int c = 0; c < b; ++c) Q[r * b + c] = (r == c) ? 1.0 : 0.0;
+    // Q (global, b x b) accumulates the rotations
+    for (int e = tid; e < b * b; e += nt) Q[e] = (e / b == e % b) ? 1.0 : 0.0;
     __syncthreads();
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (tid == 0) {
             double off = 0.0, tot = 0.0;
-            for (int r = 0; r < b; ++r)
-                for (int c = 0; c < b; ++c) {
-                    tot += A[r][c] * A[r][c];
-                    if (r != c) off += A[r][c] * A[r][c];
+            for (int r = 0; r < bp; ++r)
+                for (int c = 0; c < bp; ++c) {
+                    const double x = A[r][c] * A[r][c];
+                    tot += x;
+                    if (r != c) off += x;
                 }
             done = off <= 1e-30 * tot || tot == 0.0;
         }
         __syncthreads();
         if (done) break;
-        for (int pp = 0; pp < b - 1; ++pp) {
-            for (int qq = pp + 1; qq < b; ++qq) {
+        for (int step = 0; step < bp - 1; ++step) {
+            if (tid < half) {
+                // circle method: index 0 fixed, 1..bp-1 rotate
+                int p, q;
                 if (tid == 0) {
-                    const double apq = A[pp][qq];
-                    double c = 1.0, s = 0.0;
-                    if (apq != 0.0) {
-                        const double theta = (A[qq][qq] - A[pp][pp]) / (2.0 * apq);
-                        const double t = (theta >= 0 ? 1.0 : -1.0) /
-                                         (fabs(theta) + sqrt(theta * theta + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        s = t * c;
-                    }
-                    cs[0] = c;
-                    cs[1] = s;
+                    p = 0;
+                    q = 1 + step % (bp - 1);
+                } else {
+                    p = 1 + (step + tid) % (bp - 1);
+                    q = 1 + (step - tid + (bp - 1)) % (bp - 1);
                 }
-                __syncthreads();
-                const double c = cs[0], s = cs[1];
-                if (s != 0.0) {
-                    // A <- J^T A J with J the rotation in the (pp, qq) plane
-                    for (int r = tid; r < b; r += blockDim.x) {
-                        const double arp = A[r][pp], arq = A[r][qq];
-                        A[r][pp] = c * arp - s * arq;
-                        A[r][qq] = s * arp + c * arq;
-                    }
-                    __syncthreads();
-                    for (int r = tid; r < b; r += blockDim.x) {
-                        const double apr = A[pp][r], aqr = A[qq][r];
-                        A[pp][r] = c * apr - s * aqr;
-                        A[qq][r] = s * apr + c * aqr;
-                        const double vrp = Q[r * b + pp], vrq = Q[r * b + qq];
-                        Q[r * b + pp] = c * vrp - s * vrq;
-                        Q[r * b + qq] = s * vrp + c * vrq;
-                    }
+                const double apq = A[p][q];
+                double c = 1.0, sn = 0.0;
+                if (apq != 0.0) {
+                    const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+                    const double t = (theta >= 0 ? 1.0 : -1.0) /
+                                     (fabs(theta) + sqrt(theta * theta + 1.0));
+                    c = 1.0 / sqrt(t * t + 1.0);
+                    sn = t * c;
                 }
-                __syncthreads();
+                rp[tid] = p;
+                rq[tid] = q;
+                rc[tid] = c;
+                rs[tid] = sn;
             }
+            __syncthreads();
+            // columns: A <- A J, Q <- Q J (a pair with the padding index is
+            // the identity: its 2x2 block is zero)
+            for (int w = tid; w < half * bp; w += nt) {
+                const int k = w / bp, r = w % bp;
+                const int p = rp[k], q = rq[k];
+                if (p >= b || q >= b) continue;
+                const double c = rc[k], sn = rs[k];
+                const double arp = A[r][p], arq = A[r][q];
+                A[r][p] = c * arp - sn * arq;
+                A[r][q] = sn * arp + c * arq;
+                if (r < b) {
+                    const double qrp = Q[r * b + p], qrq = Q[r * b + q];
+                    Q[r * b + p] = c * qrp - sn * qrq;
+                    Q[r * b + q] = sn * qrp + c * qrq;
+                }
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int w = tid; w < half * bp; w += nt) {
+                const int k = w / bp, r = w % bp;
+                const int p = rp[k], q = rq[k];
+                if (p >= b || q >= b) continue;
+                const double c = rc[k], sn = rs[k];
+                const double apr = A[p][r], aqr = A[q][r];
+                A[p][r] = c * apr - sn * aqr;
+                A[q][r] = sn * apr + c * aqr;
+            }
+            __syncthreads();
         }
     }
-    for (int r = tid; r < b; r += blockDim.x) lam[r] = A[r][r];
+    for (int r = tid; r < b; r += nt) lam[r] = A[r][r];
 }
 
 // U[c*pt + i] = sum_q V[q*pt + i] Q[q*b + order[c]] for the k largest lambda,
@@ -307,12 +337,23 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     Ws w = carve(work, pt, b);
     const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
     const int pblocks = (int)((pt + 63) / 64);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t jsplit = (2LL * sms + pblocks - 1) / pblocks;
+    if (jsplit > (pt + 31) / 32) jsplit = (pt + 31) / 32;
+    if (jsplit < 1) jsplit = 1;
+    int64_t jlen = (pt + jsplit - 1) / jsplit;
+    jlen = (jlen + 31) / 32 * 32;
+    jsplit = (pt + jlen - 1) / jlen;
+    const dim3 pgrid((unsigned)pblocks, (unsigned)jsplit);
     int eblocks = (int)((b * pt + 255) / 256);
     if (eblocks > 4096) eblocks = 4096;
     int ablocks = (int)((pt + 127) / 128);
     init_v_kernel<<<eblocks, 256, 0, s>>>(w.V, pt, b, k0, k1);
     for (int it = 0; it <= iters; ++it) {
-        panel_kernel<<<pblocks, 256, 0, s>>>(C, w.V, pt, b, w.W);
+        cudaMemsetAsync(w.W, 0, (size_t)b * pt * sizeof(double), s);
+        panel_kernel<<<pgrid, 256, 0, s>>>(C, w.V, pt, b, jlen, w.W);
         if (it == iters) break;
         small_gram_kernel<<<b * b, 256, 0, s>>>(w.W, w.W, pt, b, w.Gm);
         chol_inv_kernel<<<1, 64, 0, s>>>(w.Gm, b, w.Rinv);
@@ -320,7 +361,7 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     }
     // Rayleigh-Ritz: H = V^T (C V)
     small_gram_kernel<<<b * b, 256, 0, s>>>(w.V, w.W, pt, b, w.H);
-    jacobi_kernel<<<1, 64, 0, s>>>(w.H, b, w.Q, w.lam);
+    jacobi_kernel<<<1, 256, 0, s>>>(w.H, b, w.Q, w.lam);
     ritz_out_kernel<<<k, 256, 0, s>>>(w.V, w.Q, w.lam, pt, b, k, U, evals);
     return cudaGetLastError();
 }
