@@ -329,10 +329,17 @@ def run_gpu(args, cfg):
                     "peak": None, "unit": "Gproducts/s", "frac": None, "traffic": None,
                     "note": f"shared-memory atomic scatter over {ntile} tiles"}
         else:
-            flops = 2.0 * n * pt * pt * (3 if args.gram == "bf16x3" else 1)
+            # tensor-core work actually issued: 128 x N upper tiles over n rows,
+            # three products per tile for the split mode
+            N = 256 if pt >= 256 else pt
+            ntiles = sum(pt // N - bi // (N // 128) for bi in range(pt // 128))
+            prods = 3 if args.gram == "bf16x3" else 1
+            flops = 2.0 * n * 128 * N * ntiles * prods
             ach = flops / (stage_ms["gram"] * 1e-3) / 1e12
             roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": ach,
                     "peak": bf16s, "unit": "TFLOP/s", "frac": ach / bf16s, "traffic": None,
+                    "flops_per_launch": flops, "tiles": ntiles,
+                    "algorithmic_macs": n * m * (m + 1) / 2,
                     "peak_source": f"{peak_src} bf16_tflops_sustained"}
 
     # ---- end to end through the C ABI with host buffers

@@ -152,6 +152,21 @@ sk_status sk_kmeans_step(const sk_ctx *ctx, const int32_t *idx, const float *val
                          float *dist, double *S, int32_t *cnt, int64_t *nk,
                          void *stream);
 
+/* Fused pass with incremental sums: assignment against mu (as
+ * sk_kmeans_assign) and an exact update of the running sums.  On entry,
+ * labels (device int32 n) hold each row's previous cluster (or -1) and S, cnt,
+ * nk hold the sums of Eq. (mu_update_one) for those labels (as left by
+ * sk_kmeans_step or a previous call); a row whose label changes from c to c'
+ * is subtracted from cluster c and added to c'.  On return labels, S, cnt, nk
+ * describe the new assignment.  changed (device int64 scalar, or NULL) is
+ * incremented by the number of rows whose label changed.  After the first
+ * pass few labels change, so later passes do little more than the
+ * assignment. */
+sk_status sk_kmeans_step_delta(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                               int64_t n, const float *mu, int32_t K, int32_t *labels,
+                               float *dist, double *S, int32_t *cnt, int64_t *nk,
+                               int64_t *changed, void *stream);
+
 /* Centre update (Eq. (mu_update_two)): mu[k*pt + j] = S/cnt where cnt > 0;
  * a coordinate no row of cluster k sampled cannot be estimated and keeps its
  * previous value (an empty cluster keeps its whole centre).  mu: device

@@ -61,6 +61,7 @@ def load(path: str | None = None):
             "sk_kmeans_assign": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp]),
             "sk_kmeans_update": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp]),
             "sk_kmeans_step": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),
+            "sk_kmeans_step_delta": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
             "sk_kmeans_finalize": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_unmix": (st, [vp, vp, i64, vp, vp]),
             "sk_unmix_f64": (st, [vp, vp, i64, vp, vp]),
@@ -260,6 +261,16 @@ def sk_kmeans_step(ctx: Ctx, idx, val, mu, labels, S, cnt, nk, dist=None, stream
     _check("sk_kmeans_step", load().sk_kmeans_step(ctx.handle, _ptr(idx), _ptr(val), n, _ptr(mu),
                                                    K, _ptr(labels), _ptr(dist), _ptr(S),
                                                    _ptr(cnt), _ptr(nk), _stream(stream)))
+    return labels
+
+
+def sk_kmeans_step_delta(ctx: Ctx, idx, val, mu, labels, S, cnt, nk, dist=None, changed=None,
+                         stream=None):
+    n = idx.shape[0]
+    K = mu.shape[0]
+    _check("sk_kmeans_step_delta", load().sk_kmeans_step_delta(
+        ctx.handle, _ptr(idx), _ptr(val), n, _ptr(mu), K, _ptr(labels), _ptr(dist), _ptr(S),
+        _ptr(cnt), _ptr(nk), _ptr(changed), _stream(stream)))
     return labels
 
 

@@ -133,16 +133,71 @@ __device__ __forceinline__ int yaddr(int ebase, int c) {
     }
 }
 
+// Packed FP32 pairs (two independent IEEE round-to-nearest operations each).
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float lo2(uint64_t a) { return __uint_as_float((uint32_t)a); }
+__device__ __forceinline__ float hi2(uint64_t a) { return __uint_as_float((uint32_t)(a >> 32)); }
+
+// Butterfly stage on bit rb of the 32-element register index r (element r is
+// component r&1 of pair r>>1): rb = 0 pairs the two halves of one register
+// pair, rb >= 1 pairs whole register pairs with packed add/sub.
+template <int NPAIR>
+__device__ __forceinline__ void wht_stage(uint64_t (&w)[NPAIR], int rb) {
+    if (rb == 0) {
+#pragma unroll
+        for (int P = 0; P < NPAIR; ++P) {
+            const float a = lo2(w[P]), b = hi2(w[P]);
+            w[P] = pk2(a + b, a - b);
+        }
+    } else {
+        const int pb = 1 << (rb - 1);
+#pragma unroll
+        for (int P = 0; P < NPAIR; ++P) {
+            if (!(P & pb)) {
+                uint64_t sm, df;
+                asm("add.rn.f32x2 %0, %1, %2;" : "=l"(sm) : "l"(w[P]), "l"(w[P | pb]));
+                asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(w[P]), "l"(w[P | pb]));
+                w[P] = sm;
+                w[P | pb] = df;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int readA(const uint32_t *A, uint32_t tag, int j) {
     const uint32_t a = A[j];
     return (a >> 16) == tag ? (int)(a & 0xFFFFu) : j;
+}
+
+// Window of the row's mask-word stream: two batches of 128 words (one
+// Philox block per lane per batch), batch b in slot b & 1.
+struct WordWindow {
+    uint32_t *words;  // 256 words of shared memory
+    int have0, have1; // batch held by slot 0 / slot 1 (-1: none)
+};
+
+__device__ __forceinline__ void ensure_batches(WordWindow &ww, const CompressParams &P, uint64_t g,
+                                               uint32_t wlo, uint32_t whi, int lane) {
+    for (uint32_t b = wlo >> 7; b <= (whi >> 7); ++b) {
+        int &have = (b & 1) ? ww.have1 : ww.have0;
+        if (have == (int)b) continue;
+        const uint4 o = philox4x32_10(
+            make_uint4(b * 32u + (uint32_t)lane, (uint32_t)g, (uint32_t)(g >> 32), kTagMask), P.k0,
+            P.k1);
+        __syncwarp();
+        *reinterpret_cast<uint4 *>(ww.words + (b & 1) * 128 + 4 * lane) = o;
+        __syncwarp();
+        have = (int)b;
+    }
 }
 
 // Mask of one row and its ELL gather, by one warp.
 template <int L>
 __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
                                            const float *ybuf, int ebase, uint32_t *A,
-                                           uint32_t *hit, uint32_t tag, int lane) {
+                                           uint32_t *hit, uint32_t *words, uint32_t tag, int lane) {
     constexpr int PT = 1 << L;
     const uint64_t g = (uint64_t)(P.row0 + i);
     const int m = P.m;
@@ -151,14 +206,17 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
     const unsigned lt = lanemask_lt();
     const unsigned gt = lanemask_gt();
     uint32_t woff = 0;
+    WordWindow ww{words, -1, -1};
     for (int c0 = 0; c0 < m; c0 += 32) {
         const int t = c0 + lane;
         const bool act = t < m;
         const uint32_t s = (uint32_t)(PT - t);
         uint32_t w = (uint32_t)t + woff;
         uint64_t prod = 0;
+        uint32_t wtop = (uint32_t)c0 + woff + 31;
+        ensure_batches(ww, P, g, (uint32_t)c0 + woff, wtop, lane);
         for (;;) {
-            const uint32_t word = act ? mask_word(P.k0, P.k1, g, w) : 0u;
+            const uint32_t word = act ? words[((w >> 7) & 1) * 128 + (w & 127)] : 0u;
             prod = (uint64_t)word * (uint64_t)s;
             bool rej = false;
             if (act && (uint32_t)prod < s) rej = (uint32_t)prod < ((0u - s) % s);
@@ -167,6 +225,8 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
             const int first = __ffs(bal) - 1;
             if (lane >= first) ++w;
             ++woff;
+            ++wtop;
+            ensure_batches(ww, P, g, (uint32_t)c0 + woff, wtop, lane);
         }
         const int k = act ? t + (int)(prod >> 32) : -1 - lane;
         const unsigned grpm = __match_any_sync(kFull, k);
@@ -221,6 +281,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
     uint32_t *hit = reinterpret_cast<uint32_t *>(after + (size_t)NG * PT * 4) + grp * 32;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(after + (size_t)NG * PT * 4 + NG * 32 * 4) +
                      warp * kNB;
+    uint32_t *words = reinterpret_cast<uint32_t *>(after + (size_t)NG * PT * 4 + NG * 32 * 4 +
+                                                   (size_t)kWarps * kNB * 8) +
+                      warp * 256;
 
     if constexpr (!DENSE) {
         if (wg == 0)
@@ -324,24 +387,19 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
             }
         }
         }
-        // ---- D: flip the sign bit where D_j = -1
+        // ---- D: flip the sign bit where D_j = -1; pack into register pairs
+        uint64_t w2[16];
 #pragma unroll
-        for (int r = 0; r < 32; ++r)
-            v[r] = __uint_as_float(__float_as_uint(v[r]) ^ (((smask >> r) & 1u) << 31));
+        for (int P2 = 0; P2 < 16; ++P2) {
+            const uint32_t a = __float_as_uint(v[2 * P2]) ^ (((smask >> (2 * P2)) & 1u) << 31);
+            const uint32_t b = __float_as_uint(v[2 * P2 + 1]) ^ (((smask >> (2 * P2 + 1)) & 1u) << 31);
+            w2[P2] = ((uint64_t)b << 32) | a;
+        }
         // ---- phase A: register bit rb <-> element bit {0,1,7,8,9}[rb]
 #pragma unroll
         for (int rb = 0; rb < 5; ++rb) {
             const int eb = rb < 2 ? rb : rb + 5;
-            if (eb < L) {
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    if (!(r & (1 << rb))) {
-                        const float a = v[r], b = v[r | (1 << rb)];
-                        v[r] = a + b;
-                        v[r | (1 << rb)] = a - b;
-                    }
-                }
-            }
+            if (eb < L) wht_stage<16>(w2, rb);
         }
         // every lane has read its samples (TMA) / previous gathers are done
         group_sync<G>(grp);
@@ -350,29 +408,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
         for (int ip = 0; ip < 8; ++ip) {
             const int e = 128 * ip + 4 * lane;
             *reinterpret_cast<float4 *>(wbuf + phys(e)) =
-                make_float4(v[4 * ip], v[4 * ip + 1], v[4 * ip + 2], v[4 * ip + 3]);
+                make_float4(lo2(w2[2 * ip]), hi2(w2[2 * ip]), lo2(w2[2 * ip + 1]), hi2(w2[2 * ip + 1]));
         }
         __syncwarp();
         // ---- phase B: lane = (q, i''), register j <-> element bits 2..6
         {
             const int q = lane & 3, ib = lane >> 2;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = wbuf[phys(128 * ib + 4 * j + q)];
+            for (int P2 = 0; P2 < 16; ++P2)
+                w2[P2] = pk2(wbuf[phys(128 * ib + 4 * (2 * P2) + q)],
+                             wbuf[phys(128 * ib + 4 * (2 * P2 + 1) + q)]);
 #pragma unroll
-            for (int rb = 0; rb < 5; ++rb) {
-                if (rb + 2 < L) {
+            for (int rb = 0; rb < 5; ++rb)
+                if (rb + 2 < L) wht_stage<16>(w2, rb);
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) {
-                        if (!(r & (1 << rb))) {
-                            const float a = v[r], b = v[r | (1 << rb)];
-                            v[r] = a + b;
-                            v[r | (1 << rb)] = a - b;
-                        }
-                    }
-                }
+            for (int P2 = 0; P2 < 16; ++P2) {
+                wbuf[phys(128 * ib + 4 * (2 * P2) + q)] = lo2(w2[P2]);
+                wbuf[phys(128 * ib + 4 * (2 * P2 + 1) + q)] = hi2(w2[P2]);
             }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) wbuf[phys(128 * ib + 4 * j + q)] = v[j];
         }
         // ---- phase C (pt > 1024): element bits 10.. across the group's warps
         if constexpr (L > 10) {
@@ -380,26 +433,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
             group_sync<G>(grp);
             const int tau = wg * 32 + lane;
 #pragma unroll
-            for (int s = 0; s < S; ++s)
+            for (int s2 = 0; s2 < S; ++s2)
 #pragma unroll
-                for (int w2 = 0; w2 < G; ++w2)
-                    v[s * G + w2] = ybuf[1024 * w2 + phys(tau + 32 * G * s)];
+                for (int w3 = 0; w3 < G; w3 += 2)
+                    w2[(s2 * G + w3) >> 1] = pk2(ybuf[1024 * w3 + phys(tau + 32 * G * s2)],
+                                                 ybuf[1024 * (w3 + 1) + phys(tau + 32 * G * s2)]);
 #pragma unroll
-            for (int rb = 0; (1 << rb) < G; ++rb) {
+            for (int rb = 0; (1 << rb) < G; ++rb) wht_stage<16>(w2, rb);
 #pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    if (!(r & (1 << rb))) {
-                        const float a = v[r], b = v[r | (1 << rb)];
-                        v[r] = a + b;
-                        v[r | (1 << rb)] = a - b;
-                    }
+            for (int s2 = 0; s2 < S; ++s2)
+#pragma unroll
+                for (int w3 = 0; w3 < G; w3 += 2) {
+                    ybuf[1024 * w3 + phys(tau + 32 * G * s2)] = lo2(w2[(s2 * G + w3) >> 1]);
+                    ybuf[1024 * (w3 + 1) + phys(tau + 32 * G * s2)] = hi2(w2[(s2 * G + w3) >> 1]);
                 }
-            }
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-#pragma unroll
-                for (int w2 = 0; w2 < G; ++w2)
-                    ybuf[1024 * w2 + phys(tau + 32 * G * s)] = v[s * G + w2];
         }
         group_sync<G>(grp);
 
@@ -424,7 +471,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
                 for (int b = 0; b < RPU; ++b) {
                     const int64_t i = r0 + b;
                     if (i >= P.n) break;
-                    sample_row<L>(P, i, ybuf, b * PT, A, hit, tag, lane);
+                    sample_row<L>(P, i, ybuf, b * PT, A, hit, words, tag, lane);
                     if (++tag == 0x10000u) {
                         for (int j = lane; j < PT; j += 32) A[j] = 0u;
                         __syncwarp();
@@ -445,7 +492,7 @@ cudaError_t launch_LT(const CompressParams &P, cudaStream_t s) {
     constexpr int BUF = (L <= 10) ? 1024 : PT;
     constexpr int NBUF = TMA ? kNB : 1;
     const size_t smem = (size_t)NG * NBUF * BUF * 4 + (size_t)NG * PT * 4 + NG * 32 * 4 +
-                        (size_t)kWarps * kNB * 8;
+                        (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4;
     auto kern = compress_kernel<L, DENSE, TMA>;
     cudaError_t e0 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);

@@ -36,7 +36,9 @@ struct KmParams {
     double *S;
     int32_t *cnt;
     int64_t *nk;
-    int do_assign, do_update;
+    unsigned long long *changed;  // delta mode: rows whose label changed (may be NULL)
+    int do_assign;
+    int do_update;  // 0 none, 1 full sums, 2 incremental (changed rows only)
 };
 
 // Packed FP32 pairs (two independent IEEE round-to-nearest operations).
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     float *sS = reinterpret_cast<float *>(smem_raw + off);
     int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
     int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
-    if (PRIV && P.do_update) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
+    if (PRIV && P.do_update == 1) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
     int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + off);
 
     const int tid = threadIdx.x;
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
         }
     }
-    if (PRIV && P.do_update) {
+    if (PRIV && P.do_update == 1) {
         for (int e = tid; e < KP; e += blockDim.x) {
             sS[e] = 0.f;
             sC[e] = 0;
@@ -177,12 +179,56 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             bd = __shfl_sync(kFull, bd, leadl);
             bk = __shfl_sync(kFull, bk, leadl);
             label = bk;
+            int old = -1;
             if (row_ok && kl == 0) {
+                if (P.do_update == 2) old = P.labels[i];
                 P.labels[i] = label;
                 if (P.dist) P.dist[i] = bd;
             }
+            if (P.do_update == 2) {
+                // incremental sums: a row whose label moved from old to label
+                // leaves cluster old and joins cluster label (exact in FP64 for
+                // float inputs up to rounding of the running sums)
+                old = __shfl_sync(kFull, old, (lead < 32) ? lead : lane);
+                const bool moved = row_ok && kl == 0 && old != label;
+                const unsigned mv = __ballot_sync(kFull, moved);
+                if (P.changed && lane == 0 && mv)
+                    atomicAdd(P.changed, (unsigned long long)__popc(mv));
+                unsigned pending = mv;
+                while (pending) {
+                    const int src = __ffs(pending) - 1;
+                    pending &= pending - 1;
+                    const int rs = src / P.LPR;
+                    const int newl = __shfl_sync(kFull, label, src);
+                    const int oldl = __shfl_sync(kFull, old, src);
+                    for (int t = lane; t < m; t += 32) {
+                        int j;
+                        float v;
+                        if constexpr (STAGE) {
+                            const int2 iv = stage[rs * m + t];
+                            j = iv.x & pmask;
+                            v = __int_as_float(iv.y);
+                        } else {
+                            j = __ldg(P.idx + (base + rs) * m + t) & pmask;
+                            v = __ldg(P.val + (base + rs) * m + t);
+                        }
+                        atomicAdd(P.S + (int64_t)newl * P.pt + j, (double)v);
+                        atomicAdd(P.cnt + (int64_t)newl * P.pt + j, 1);
+                        if ((unsigned)oldl < (unsigned)P.K) {
+                            atomicAdd(P.S + (int64_t)oldl * P.pt + j, -(double)v);
+                            atomicAdd(P.cnt + (int64_t)oldl * P.pt + j, -1);
+                        }
+                    }
+                    if (lane == 0) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + newl), 1ull);
+                        if ((unsigned)oldl < (unsigned)P.K)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + oldl),
+                                      (unsigned long long)(-1LL));
+                    }
+                }
+            }
         }
-        if (P.do_update) {
+        if (P.do_update == 1) {
             for (int rs = 0; rs < rows_here; ++rs) {
                 int lab;
                 if (P.do_assign) {
@@ -223,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
         }
         if constexpr (STAGE) __syncwarp();  // stage is rewritten by the next pass
     }
-    if (PRIV && P.do_update) {
+    if (PRIV && P.do_update == 1) {
         __syncthreads();
         for (int e = tid; e < KP; e += blockDim.x) {
             const int c = sC[e];
@@ -287,7 +333,7 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t mu_b = P.do_assign ? (size_t)P.pt * P.Kpad * 4 : 0;
     const size_t priv_b =
-        P.do_update ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
+        P.do_update == 1 ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
     const size_t budget = (size_t)smem_max;
     if (mu_b + priv_b <= budget) return launch_stage<KPL, true, true>(P, mu_b + priv_b, budget, s);
     if (mu_b <= budget) return launch_stage<KPL, true, false>(P, mu_b, budget, s);
@@ -300,7 +346,7 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
 cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
                           int64_t n, const float *mu, int K, int32_t *labels, float *dist,
                           double *S, int32_t *cnt, int64_t *nk, bool do_assign,
-                          bool do_update, cudaStream_t s) {
+                          int do_update, int64_t *changed, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     KmParams P;
     P.idx = idx;
@@ -317,6 +363,7 @@ cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
     P.nk = nk;
     P.do_assign = do_assign;
     P.do_update = do_update;
+    P.changed = reinterpret_cast<unsigned long long *>(changed);
     if (K <= 64) return launch_kpl<2>(P, s);
     if (K <= 128) return launch_kpl<4>(P, s);
     return launch_kpl<8>(P, s);

@@ -172,7 +172,7 @@ sk_status sk_kmeans_assign(const sk_ctx *ctx, const int32_t *idx, const float *v
     if (n == 0) return SK_OK;
     if (!mu || !labels) return fail(SK_EINVAL, "sk_kmeans_assign: NULL buffer");
     return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, mu, K, labels, dist, nullptr,
-                                         nullptr, nullptr, true, false, as_stream(stream)),
+                                         nullptr, nullptr, true, 0, nullptr, as_stream(stream)),
                        "sk_kmeans_assign");
 }
 
@@ -185,7 +185,7 @@ sk_status sk_kmeans_update(const sk_ctx *ctx, const int32_t *idx, const float *v
     if (!labels || !S || !cnt || !nk) return fail(SK_EINVAL, "sk_kmeans_update: NULL buffer");
     return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, nullptr, K,
                                          const_cast<int32_t *>(labels), nullptr, S, cnt, nk,
-                                         false, true, as_stream(stream)),
+                                         false, 1, nullptr, as_stream(stream)),
                        "sk_kmeans_update");
 }
 
@@ -197,8 +197,22 @@ sk_status sk_kmeans_step(const sk_ctx *ctx, const int32_t *idx, const float *val
     if (n == 0) return SK_OK;
     if (!mu || !labels || !S || !cnt || !nk) return fail(SK_EINVAL, "sk_kmeans_step: NULL buffer");
     return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, mu, K, labels, dist, S, cnt, nk, true,
-                                         true, as_stream(stream)),
+                                         1, nullptr, as_stream(stream)),
                        "sk_kmeans_step");
+}
+
+sk_status sk_kmeans_step_delta(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                               int64_t n, const float *mu, int32_t K, int32_t *labels, float *dist,
+                               double *S, int32_t *cnt, int64_t *nk, int64_t *changed,
+                               void *stream) {
+    sk_status st = kmeans_common("sk_kmeans_step_delta", ctx, idx, val, n, K);
+    if (st != SK_OK) return st;
+    if (n == 0) return SK_OK;
+    if (!mu || !labels || !S || !cnt || !nk)
+        return fail(SK_EINVAL, "sk_kmeans_step_delta: NULL buffer");
+    return cuda_status(sk::launch_kmeans(*ctx, idx, val, n, mu, K, labels, dist, S, cnt, nk, true,
+                                         2, changed, as_stream(stream)),
+                       "sk_kmeans_step_delta");
 }
 
 sk_status sk_kmeans_finalize(const sk_ctx *ctx, int32_t K, const double *S, const int32_t *cnt,

@@ -82,7 +82,7 @@ cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t 
 cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
                           int64_t n, const float *mu, int K, int32_t *labels, float *dist,
                           double *S, int32_t *cnt, int64_t *nk, bool do_assign,
-                          bool do_update, cudaStream_t s);
+                          int do_update, int64_t *changed, cudaStream_t s);
 cudaError_t launch_kmeans_finalize(const sk_ctx &c, int K, const double *S,
                                    const int32_t *cnt, float *mu, cudaStream_t s);
 cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *val,

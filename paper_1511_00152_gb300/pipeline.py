@@ -21,15 +21,24 @@ class KMeansState:
         self.S = torch.empty((K, ctx.pt), dtype=torch.float64, device=device)
         self.cnt = torch.empty((K, ctx.pt), dtype=torch.int32, device=device)
         self.nk = torch.empty(K, dtype=torch.int64, device=device)
+        self.changed = torch.zeros(1, dtype=torch.int64, device=device)
+        self.incremental = True
         self.graph = None
         self._graph_args = None
 
-    def iteration(self, idx, val, stream=None):
-        """One assign + update pass (Eqs. (assignments), (mu_update_two))."""
+    def iteration(self, idx, val, first: bool = True, stream=None):
+        """One assign + update pass (Eqs. (assignments), (mu_update_two)).
+
+        The first pass builds the sums from scratch; later passes update them
+        incrementally from the rows whose label changed (same sums)."""
         ctx = self.ctx
-        sk.sk_kmeans_reset(ctx, self.S, self.cnt, self.nk, stream=stream)
-        sk.sk_kmeans_step(ctx, idx, val, self.mu, self.labels, self.S, self.cnt, self.nk,
-                          dist=self.dist, stream=stream)
+        if first or not self.incremental:
+            sk.sk_kmeans_reset(ctx, self.S, self.cnt, self.nk, stream=stream)
+            sk.sk_kmeans_step(ctx, idx, val, self.mu, self.labels, self.S, self.cnt, self.nk,
+                              dist=self.dist, stream=stream)
+        else:
+            sk.sk_kmeans_step_delta(ctx, idx, val, self.mu, self.labels, self.S, self.cnt,
+                                    self.nk, dist=self.dist, changed=self.changed, stream=stream)
         sk.sk_kmeans_finalize(ctx, self.S, self.cnt, self.mu, stream=stream)
 
     def run(self, idx, val, mu0, iters: int, use_graph: bool = True):
@@ -39,8 +48,8 @@ class KMeansState:
         (the same kernels, one launch for the whole loop)."""
         self.mu.copy_(mu0)
         if not use_graph or iters == 0:
-            for _ in range(iters):
-                self.iteration(idx, val)
+            for it in range(iters):
+                self.iteration(idx, val, first=(it == 0))
             return self.labels, self.mu
         key = (idx.data_ptr(), val.data_ptr(), idx.shape[0], iters)
         if self.graph is None or self._graph_args != key:
@@ -49,13 +58,14 @@ class KMeansState:
             s.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(s):
                 saved = self.mu.clone()
-                self.iteration(idx, val, stream=s)
+                self.iteration(idx, val, first=True, stream=s)
+                self.iteration(idx, val, first=False, stream=s)
                 self.mu.copy_(saved)
             torch.cuda.current_stream().wait_stream(s)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
-                for _ in range(iters):
-                    self.iteration(idx, val)
+                for it in range(iters):
+                    self.iteration(idx, val, first=(it == 0))
             self.graph, self._graph_args = g, key
             self.mu.copy_(mu0)
         self.graph.replay()

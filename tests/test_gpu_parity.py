@@ -317,3 +317,40 @@ def test_invalid_arguments_rejected_before_launch(sk):
     assert lib.sk_cov_topk(ctx2.handle, sk._ptr(G), 0, 10, nul, nul, nul, nul) == sk.SK_EINVAL
     assert "must be" in sk.sk_last_error() or sk.sk_last_error() != ""
     assert sk.sk_device_status() == sk.SK_OK
+
+
+@pytest.mark.parametrize("p,m,n,K", [(64, 8, 2000, 5), (1024, 51, 20000, 10), (256, 5, 5000, 50)])
+def test_kmeans_incremental_sums_match_recomputed(sk, p, m, n, K):
+    """sk_kmeans_step_delta keeps S, cnt, nk equal to the sums of
+    Eq. (mu_update_one) for the current labels: counts exactly, sums to FP64
+    rounding; the run matches the from-scratch loop."""
+    from paper_1511_00152_gb300 import pipeline
+    X = synth.mixture(n, p, min(K, 10), seed=p + n)[0]
+    seed = 29
+    ctx = sk.sk_init(p, m, seed)
+    Xd = _dev(X)
+    idx, val = sk.sk_compress(ctx, Xd)
+    rows = synth.init_rows(n, K, seed)
+    mu0 = pipeline.initial_centres(ctx, Xd, rows)
+    a = pipeline.KMeansState(ctx, n, K)
+    la, mua = a.run(idx, val, mu0, iters=8, use_graph=False)
+    b = pipeline.KMeansState(ctx, n, K)
+    b.incremental = False
+    lb, mub = b.run(idx, val, mu0, iters=8, use_graph=False)
+    torch.cuda.synchronize()
+    agree = float((la == lb).float().mean())
+    assert agree >= 0.999, agree
+    if agree == 1.0:
+        assert torch.allclose(mua, mub, rtol=1e-5, atol=1e-6)
+    # the running sums describe the final labels exactly
+    oi = idx.cpu().numpy()
+    ov = val.cpu().numpy().astype(np.float64)
+    labs = a.labels.cpu().numpy()
+    mu_prev = np.zeros((K, ctx.pt))
+    _mu, counts_o, nk_o = oracle.kmeans_update(oi, ov, labs, mu_prev, ctx.pt)
+    assert np.array_equal(a.cnt.cpu().numpy(), counts_o)
+    assert np.array_equal(a.nk.cpu().numpy(), nk_o)
+    # the first pass sums per-CTA float partials, later passes add FP64 deltas
+    So = np.where(counts_o > 0, _mu * counts_o, 0.0)
+    assert np.abs(a.S.cpu().numpy() - So).max() <= 1e-5 * (np.abs(So).max() + 1e-30)
+    assert int(a.changed.item()) > 0
