@@ -125,6 +125,25 @@ sk_status sk_cov_topk(const sk_ctx *ctx, const double *C, int32_t k, int32_t ite
                       double *evals, double *U, double *work, void *stream);
 int64_t sk_cov_topk_workspace(int64_t pt, int32_t k);
 
+/* sk_cov_topk for callers that cannot allocate device memory: the same
+ * computation, with its scratch in a fixed array of 4 MiB (524,288 doubles)
+ * inside the library instead of a caller workspace.  (No counterpart in the
+ * paper; this is a deployment convenience.)  Meant for code that may not call
+ * cudaMalloc or any allocating library routine: an application whose device
+ * memory is owned entirely by its own caching allocator, or a latency-critical
+ * loop that cannot afford an allocation's implicit device synchronisation.
+ * The call allocates nothing; the caller still provides C, evals and U as for
+ * sk_cov_topk.  Shapes whose scratch, sk_cov_topk_workspace(pt, k), exceeds
+ * 524,288 doubles (for example pt = 8192 with k > 15) are rejected with
+ * SK_EUNSUPPORTED before anything is enqueued.  Every GPU that loads the
+ * library holds the array until the process exits.  The first call on a
+ * device (with that device current) looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the one array
+ * and leave their intermediate results in it: calls whose work overlaps on the
+ * GPU (different streams without ordering) race and must not be issued. */
+sk_status sk_cov_topk_static(const sk_ctx *ctx, const double *C, int32_t k, int32_t iters,
+                             double *evals, double *U, void *stream);
+
 /* Sparsified K-means assignment (Sec. VI-B, Eq. (assignments)): for each
  * ELL row i, labels[i] = argmin_k sum_t (val[i,t] - mu[k, idx[i,t]])^2 with
  * ties going to the smallest k, the restricted squared distance computed

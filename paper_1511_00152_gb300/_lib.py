@@ -58,6 +58,7 @@ def load(path: str | None = None):
             "sk_kmeans_reset": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_cov_topk": (st, [vp, vp, i32, i32, vp, vp, vp, vp]),
             "sk_cov_topk_workspace": (i64, [i64, i32]),
+            "sk_cov_topk_static": (st, [vp, vp, i32, i32, vp, vp, vp]),
             "sk_kmeans_assign": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp]),
             "sk_kmeans_update": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp]),
             "sk_kmeans_step": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),

@@ -154,6 +154,28 @@ sk_status sk_cov_topk(const sk_ctx *ctx, const double *C, int32_t k, int32_t ite
                        "sk_cov_topk");
 }
 
+sk_status sk_cov_topk_static(const sk_ctx *ctx, const double *C, int32_t k, int32_t iters,
+                             double *evals, double *U, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (k < 1 || k > 64 || k > ctx->pt)
+        return fail(SK_EINVAL, "sk_cov_topk_static: k = %d must be in [1, min(pt, 64)]", k);
+    if (iters < 0 || iters > 100000)
+        return fail(SK_EINVAL, "sk_cov_topk_static: iters out of range");
+    if (!C || !evals || !U) return fail(SK_EINVAL, "sk_cov_topk_static: NULL buffer");
+    const int64_t need = sk::topk_workspace(ctx->pt, k);
+    const int64_t have = sk::topk_static_capacity();
+    if (need > have)
+        return fail(SK_EUNSUPPORTED,
+                    "sk_cov_topk_static: pt = %lld, k = %d needs %lld doubles of scratch; the "
+                    "fixed array holds %lld (use sk_cov_topk with a caller workspace)",
+                    (long long)ctx->pt, k, (long long)need, (long long)have);
+    double *scratch = nullptr;
+    cudaError_t e = sk::topk_static_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_status(e, "sk_cov_topk_static (scratch lookup)");
+    return cuda_status(sk::launch_topk(*ctx, C, k, iters, evals, U, scratch, as_stream(stream)),
+                       "sk_cov_topk_static");
+}
+
 static sk_status kmeans_common(const char *fn, const sk_ctx *ctx, const int32_t *idx,
                                const float *val, int64_t n, int32_t K) {
     if (!ctx) return fail(SK_EINVAL, "%s: ctx is NULL", fn);

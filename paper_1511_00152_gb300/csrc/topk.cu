@@ -10,6 +10,8 @@
 // its largest-magnitude entry positive.  Everything is float64: the panel
 // product is a tiled CUDA-core kernel, the small b x b factorisations run in
 // one CTA.
+#include <mutex>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -324,6 +326,38 @@ __global__ void ritz_out_kernel(const double *V, const double *Q, const double *
 }
 
 }  // namespace
+
+// ---- fixed scratch for callers that cannot allocate device memory
+//
+// One array per device that loads the library, held until the process exits.
+// Host code must not pass g_topk_scratch itself to a kernel (on the host the
+// name is only a stand-in for the device symbol); its device address is looked
+// up once per device with cudaGetSymbolAddress, with that device current.
+namespace {
+constexpr int64_t kTopkStaticDoubles = 512 * 1024;  // 4 MiB
+static __device__ __align__(256) double g_topk_scratch[kTopkStaticDoubles];
+std::mutex g_topk_scratch_mu;
+double *g_topk_scratch_ptr[128] = {};
+}  // namespace
+
+int64_t topk_static_capacity() { return kTopkStaticDoubles; }
+
+cudaError_t topk_static_scratch(double **out) {
+    *out = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_topk_scratch_mu);
+    if (!g_topk_scratch_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_topk_scratch);
+        if (e != cudaSuccess) return e;
+        g_topk_scratch_ptr[dev] = static_cast<double *>(ptr);
+    }
+    *out = g_topk_scratch_ptr[dev];
+    return cudaSuccess;
+}
 
 int64_t topk_workspace(int64_t pt, int k) {
     const int b = block_cols(pt, k);
