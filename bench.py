@@ -242,11 +242,12 @@ def run_gpu(args, cfg):
     Ux = torch.empty((k, p), dtype=torch.float64, device=dev)
     work = torch.empty(sk.sk_cov_topk_workspace(pt, k), dtype=torch.float64, device=dev)
     cen = torch.empty((K, p), dtype=torch.float32, device=dev)
+    gwork = torch.empty(max(1, sk.sk_cov_workspace_bytes(ctx, mode, n)), dtype=torch.uint8, device=dev)
     st = pipeline.KMeansState(ctx, n, K, device=dev)
     stream = torch.cuda.current_stream()
 
     stages = ["compress", "gram", "cov_finalize", "topk", "kmeans", "unmix"]
-    launches = {"compress": 1, "gram": 1, "cov_finalize": 1,
+    launches = {"compress": 1, "gram": 1 if args.gram == "fp32" else 2, "cov_finalize": 1,
                 "topk": 1 + (args.topk_iters + 1) + 3 * args.topk_iters + 3 + 1,
                 "kmeans": 1 + 2 * iters, "unmix": 1}
 
@@ -258,7 +259,7 @@ def run_gpu(args, cfg):
         sk.sk_compress(ctx, X, idx=idx, val=val)
         mark(1)
         sk.sk_cov_reset(ctx, G)
-        sk.sk_cov_accumulate(ctx, mode, idx, val, G)
+        sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=gwork)
         mark(2)
         sk.sk_cov_finalize(ctx, G, n, C=C)
         mark(3)
@@ -359,7 +360,7 @@ def run_gpu(args, cfg):
             X_saved = X
             sk.sk_compress(ctx, Xd2, idx=idx, val=val)
             sk.sk_cov_reset(ctx, G)
-            sk.sk_cov_accumulate(ctx, mode, idx, val, G)
+            sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=gwork)
             sk.sk_cov_finalize(ctx, G, n, C=C)
             sk.sk_cov_topk(ctx, C, k, args.topk_iters, evals=evals, U=U, work=work)
             sk.sk_unmix(ctx, U, out=Ux)

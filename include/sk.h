@@ -96,11 +96,20 @@ sk_status sk_precondition(const sk_ctx *ctx, const float *X, int64_t n, int64_t 
  * (idx, val as produced by sk_compress), w_i the pt-vector with val at idx.
  * G: device float64 pt x pt, caller-zeroed before the first call; only its
  * upper triangle (j <= k) is defined after the call, the strict lower
- * triangle holds unspecified partial sums.  mode is SK_GRAM_*.  Repeated
- * calls on chunks accumulate; the result does not depend on the chunking
- * beyond floating-point summation order. */
+ * triangle holds unspecified partial sums.  mode is SK_GRAM_*.  The tensor-core
+ * modes (pt >= 128) need a device workspace `work` of at least
+ * sk_cov_workspace_bytes(ctx, mode, n) bytes, 256-byte aligned, that they
+ * overwrite (the rows' entries regrouped by 128-column block); SK_GRAM_FP32
+ * needs none (work may be NULL).  Repeated calls on chunks accumulate; the
+ * result does not depend on the chunking beyond floating-point summation
+ * order. */
 sk_status sk_cov_accumulate(const sk_ctx *ctx, int mode, const int32_t *idx,
-                            const float *val, int64_t n, double *G, void *stream);
+                            const float *val, int64_t n, double *G, void *work,
+                            int64_t work_bytes, void *stream);
+
+/* Workspace bytes sk_cov_accumulate needs for n rows in the given mode (0 for
+ * SK_GRAM_FP32; -1 for invalid arguments). */
+int64_t sk_cov_workspace_bytes(const sk_ctx *ctx, int mode, int64_t n);
 
 /* Zeroes a pt x pt float64 Gram accumulator G (device) on the stream. */
 sk_status sk_cov_reset(const sk_ctx *ctx, double *G, void *stream);

@@ -52,7 +52,8 @@ def load(path: str | None = None):
             "sk_ptilde": (i64, [vp]),
             "sk_compress": (st, [vp, vp, i64, i64, i64, vp, vp, vp]),
             "sk_precondition": (st, [vp, vp, i64, i64, vp, vp]),
-            "sk_cov_accumulate": (st, [vp, ctypes.c_int, vp, vp, i64, vp, vp]),
+            "sk_cov_accumulate": (st, [vp, ctypes.c_int, vp, vp, i64, vp, vp, i64, vp]),
+            "sk_cov_workspace_bytes": (i64, [vp, ctypes.c_int, i64]),
             "sk_cov_finalize": (st, [vp, vp, i64, vp, vp]),
             "sk_cov_reset": (st, [vp, vp, vp]),
             "sk_kmeans_reset": (st, [vp, i32, vp, vp, vp, vp]),
@@ -174,13 +175,23 @@ def sk_precondition(ctx: Ctx, X, Y=None, stream=None):
     return Y
 
 
-def sk_cov_accumulate(ctx: Ctx, mode: int, idx, val, G, stream=None):
+def sk_cov_workspace_bytes(ctx: Ctx, mode: int, n: int) -> int:
+    return int(load().sk_cov_workspace_bytes(ctx.handle, int(mode), int(n)))
+
+
+def sk_cov_accumulate(ctx: Ctx, mode: int, idx, val, G, work=None, stream=None):
+    """G += sum of w w^T; `work` (uint8 CUDA tensor) is allocated if not given."""
     n = idx.shape[0]
     _need(idx, torch.int32, "idx", (n, ctx.m))
     _need(val, torch.float32, "val", (n, ctx.m))
     _need(G, torch.float64, "G", (ctx.pt, ctx.pt))
+    need = sk_cov_workspace_bytes(ctx, mode, n)
+    if work is None and need > 0:
+        work = torch.empty(need, dtype=torch.uint8, device=idx.device)
+    wbytes = 0 if work is None else work.numel() * work.element_size()
     _check("sk_cov_accumulate", load().sk_cov_accumulate(ctx.handle, int(mode), _ptr(idx),
-                                                         _ptr(val), n, _ptr(G), _stream(stream)))
+                                                         _ptr(val), n, _ptr(G), _ptr(work),
+                                                         wbytes, _stream(stream)))
     return G
 
 

@@ -50,8 +50,9 @@ constexpr int kProducers = kProducerWarps * 32;
 constexpr int kThreads = kProducers + 32;  // + the MMA warp
 constexpr int kSlab = 64;                  // rows per K-slab (128 bytes of BF16)
 constexpr int kTileM = 128;
-constexpr int kSegmentRows = 65536;
-constexpr int kChunk = 16;                 // entries per producer thread per chunk
+constexpr int kSegmentRows = 1 << 18;     // rows per FP32 accumulation chain (then FP64)
+constexpr int kChunk = 8;                  // bucketed entries per producer thread per pass
+constexpr int kBlk = 128;                  // column block of the bucketing
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcParams {
@@ -68,6 +69,9 @@ struct TcParams {
     int hilo;      // 1: split-BF16 (three products)
     int nstages;
     int stage_bytes;
+    int nblk;             // pt / 128 column blocks
+    const int2 *bkt;      // bucketed entries: (block << 14 | tile byte offset, value bits)
+    const int *boff;      // per slab: nblk + 1 bucket starts (relative to the slab)
     double *G;
 };
 
@@ -142,6 +146,68 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 // Byte offset of element (r, k) in a K-major, 128B-swizzled tile of 64-wide rows.
 __device__ __forceinline__ uint32_t sw_off(int r, int k) {
     return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7))) << 4) + ((k & 7) << 1));
+}
+
+// Bucketing pass: the entries of each 64-row slab (a contiguous ELL range) are
+// grouped by 128-column block; each entry carries the byte offset of its
+// (column-in-block, row-in-slab) element in a K-major, 128B-swizzled operand
+// tile, so the Gram producers only copy.  One CTA per slab; the per-block
+// counters take warp-aggregated shared-memory atomics.
+__global__ void __launch_bounds__(256) bucket_kernel(const int32_t *idx, const float *val,
+                                                     int64_t n, int m, int pt, int nblk,
+                                                     int2 *bkt, int *boff) {
+    __shared__ int hist[64];
+    __shared__ int cursor[64];
+    const int64_t s = blockIdx.x;
+    const int64_t r0 = s * kSlab;
+    const int rows = (int)((n - r0) < kSlab ? (n - r0) : kSlab);
+    const int total = rows * m;
+    const int32_t *gi = idx + r0 * m;
+    const float *gv = val + r0 * m;
+    int2 *out = bkt + s * (int64_t)kSlab * m;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned lt = lanemask_lt();
+    for (int c = tid; c < nblk; c += blockDim.x) hist[c] = 0;
+    __syncthreads();
+    for (int e0 = 0; e0 < total; e0 += blockDim.x) {
+        const int e = e0 + tid;
+        const int c = e < total ? ((__ldg(gi + e) & (pt - 1)) >> 7) : -1 - lane;
+        const unsigned grp = __match_any_sync(0xffffffffu, c);
+        if (e < total && (grp & lt) == 0u) atomicAdd(&hist[c], __popc(grp));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int c = 0; c < nblk; ++c) {
+            boff[s * (nblk + 1) + c] = acc;
+            cursor[c] = acc;
+            acc += hist[c];
+        }
+        boff[s * (nblk + 1) + nblk] = acc;
+    }
+    __syncthreads();
+    const float inv_m = 1.0f / (float)m;
+    for (int e0 = 0; e0 < total; e0 += blockDim.x) {
+        const int e = e0 + tid;
+        int j = 0, c = -1 - lane;
+        float v = 0.f;
+        if (e < total) {
+            j = __ldg(gi + e) & (pt - 1);
+            v = __ldg(gv + e);
+            c = j >> 7;
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(grp) - 1;
+        int base = 0;
+        if (e < total && lane == leader) base = atomicAdd(&cursor[c], __popc(grp));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (e < total) {
+            // row within the slab: exact (e + 0.5 is >= 0.5 from every multiple of m)
+            const int k = (int)(((float)e + 0.5f) * inv_m);
+            const int pos = base + __popc(grp & lt);
+            out[pos] = make_int2((c << 14) | (int)sw_off(j & (kBlk - 1), k), __float_as_int(v));
+        }
+    }
 }
 
 __device__ __forceinline__ void decode_tile(const TcParams &P, int t, int &bi, int &bj) {
@@ -239,45 +305,59 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
         __syncwarp();
     } else {
         // ---------------- producers (then epilogue)
-        // The entries of slab i are the contiguous ELL range [r0*m, r0*m + rows*m).
-        // They are consumed in chunks of kChunk entries per thread; the loads
-        // of the next chunk are issued before the current chunk is scattered,
-        // so the L2 latency overlaps the scatter, the stage wait and the zeroing.
+        // Slab i of the segment needs bucket bi (operand A) and buckets
+        // [bj*R, bj*R + R) (operand B, R = N / 128) of the bucketed slab; both
+        // ranges are contiguous.  The ranges of slab i + 1 are known one slab
+        // ahead and its entries are loaded into registers while slab i is
+        // scattered, so the load latency overlaps the scatter and the waits.
         const int ptid = tid;  // 0 .. kProducers-1
         const int m = P.m;
-        const float inv_m = 1.0f / (float)m;
-        const int per_chunk = kProducers * kChunk;
-        int64_t slab = 0;      // slab of the chunk held in registers
-        int pass = 0;          // chunk index within that slab
-        int cj[kChunk], nj[kChunk];
-        float cv[kChunk], nv[kChunk];
-        auto slab_total = [&](int64_t i) -> int {
-            const int64_t r0 = r_begin + i * kSlab;
-            const int64_t rows = (r_end - r0) < kSlab ? (r_end - r0) : kSlab;
-            return (int)rows * m;
+        const int R = N / kBlk;
+        const int nb1 = P.nblk + 1;
+        const int64_t slab0 = r_begin / kSlab;  // global slab index of this segment's first slab
+        struct Ranges {
+            int a0, na, b0, nb;
         };
-        auto load_chunk = [&](int64_t i, int ps, int *jj, float *vv) {
-            const int total = slab_total(i);
-            const int64_t ebase = (r_begin + i * kSlab) * (int64_t)m;
+        auto ranges = [&](int64_t i) -> Ranges {
+            const int *o = P.boff + (slab0 + i) * nb1;
+            Ranges r;
+            r.a0 = __ldg(o + bi);
+            r.na = __ldg(o + bi + 1) - r.a0;
+            r.b0 = __ldg(o + bj * R);
+            r.nb = __ldg(o + bj * R + R) - r.b0;
+            return r;
+        };
+        int ck[kChunk], cv[kChunk], nk[kChunk], nv[kChunk];
+        auto load_pass = [&](int64_t i, const Ranges &r, int ps, int *kk, int *vv) {
+            const int2 *base = P.bkt + (slab0 + i) * (int64_t)kSlab * m;
 #pragma unroll
             for (int q = 0; q < kChunk; ++q) {
-                const int e = ps * per_chunk + q * kProducers + ptid;
-                if (e < total) {
-                    jj[q] = __ldg(P.idx + ebase + e);
-                    vv[q] = __ldg(P.val + ebase + e);
-                } else {
-                    jj[q] = -1;
-                    vv[q] = 0.f;
+                const int e = ps * (kProducers * kChunk) + q * kProducers + ptid;
+                int2 x = make_int2(-1, 0);
+                if (e < r.na) {
+                    x = __ldg(base + r.a0 + e);
+                    x.x |= 1 << 30;  // operand A
+                } else if (e < r.na + r.nb) {
+                    x = __ldg(base + r.b0 + (e - r.na));
                 }
+                kk[q] = x.x;
+                vv[q] = x.y;
             }
         };
-        if (nslabs > 0) load_chunk(0, 0, cj, cv);
+        Ranges cur{0, 0, 0, 0}, nxt{0, 0, 0, 0};
+        if (nslabs > 0) {
+            cur = ranges(0);
+            load_pass(0, cur, 0, ck, cv);
+        }
+        if (nslabs > 1) nxt = ranges(1);
+        int64_t slab = 0;
+        int pass = 0;
         bool ok = true;
+        const int per_pass = kProducers * kChunk;
         while (slab < nslabs && ok) {
             const int s = (int)(slab % S);
             const uint32_t u = (uint32_t)(slab / S);
-            const int total = slab_total(slab);
-            const int npass = (total + per_chunk - 1) / per_chunk;
+            const int npass = (cur.na + cur.nb + per_pass - 1) / per_pass;
             unsigned char *st = tiles + (size_t)s * P.stage_bytes;
             if (pass == 0) {
                 if (u > 0) {
@@ -295,38 +375,42 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
                     *reinterpret_cast<uint4 *>(st + off) = make_uint4(0u, 0u, 0u, 0u);
                 named_sync(1, kProducers);
             }
-            // prefetch the next chunk (this slab's next pass, or the next slab's first)
             const bool last_pass = pass + 1 >= npass;
-            const int64_t nslab = last_pass ? slab + 1 : slab;
-            const int npass_next = last_pass ? 0 : pass + 1;
-            if (nslab < nslabs) load_chunk(nslab, npass_next, nj, nv);
+            // prefetch: the next pass of this slab, or the first pass of the next slab
+            Ranges nr = cur;
+            int64_t ns = slab;
+            int np = pass + 1;
+            if (last_pass) {
+                nr = nxt;
+                ns = slab + 1;
+                np = 0;
+            }
+            if (ns < nslabs) load_pass(ns, nr, np, nk, nv);
+            if (last_pass && slab + 2 < nslabs) nxt = ranges(slab + 2);
             unsigned char *A_hi = st, *B_hi = st + a_bytes;
             unsigned char *A_lo = st + a_bytes + b_bytes, *B_lo = A_lo + a_bytes;
 #pragma unroll
             for (int q = 0; q < kChunk; ++q) {
-                const int j = cj[q];
-                const int a = j - I0, b = j - J0;
-                const bool inA = (unsigned)a < (unsigned)kTileM;
-                const bool inB = (unsigned)b < (unsigned)N;
-                if (inA || inB) {
-                    const int e = pass * per_chunk + q * kProducers + ptid;
-                    // row within the slab: exact since e + 0.5 is at least 0.5 away
-                    // from every multiple of m and e < 2^20
-                    const int k = (int)(((float)e + 0.5f) * inv_m);
-                    const float v = cv[q];
+                const int key = ck[q];
+                if (key >= 0) {
+                    const bool isA = (key >> 30) & 1;
+                    const int c = (key >> 14) & 0xFFFF;
+                    const uint32_t off = (uint32_t)(key & 16383);
+                    const float v = __int_as_float(cv[q]);
                     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                    if (inA) *reinterpret_cast<__nv_bfloat16 *>(A_hi + sw_off(a, k)) = hi;
-                    if (inB) *reinterpret_cast<__nv_bfloat16 *>(B_hi + sw_off(b, k)) = hi;
+                    const uint32_t boffb = (uint32_t)(c - bj * R) * (kBlk * 128);
+                    unsigned char *dh = isA ? A_hi + off : B_hi + boffb + off;
+                    *reinterpret_cast<__nv_bfloat16 *>(dh) = hi;
                     if (P.hilo) {
                         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-                        if (inA) *reinterpret_cast<__nv_bfloat16 *>(A_lo + sw_off(a, k)) = lo;
-                        if (inB) *reinterpret_cast<__nv_bfloat16 *>(B_lo + sw_off(b, k)) = lo;
+                        unsigned char *dl = isA ? A_lo + off : B_lo + boffb + off;
+                        *reinterpret_cast<__nv_bfloat16 *>(dl) = lo;
                     }
                 }
             }
 #pragma unroll
             for (int q = 0; q < kChunk; ++q) {
-                cj[q] = nj[q];
+                ck[q] = nk[q];
                 cv[q] = nv[q];
             }
             if (last_pass) {
@@ -336,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
                 if (ptid == 0) mbar_arrive(smem_u32(bars + s));
                 ++slab;
                 pass = 0;
+                cur = nr;
             } else {
                 ++pass;
             }
@@ -393,8 +478,17 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
 
 }  // namespace
 
+int64_t gram_tc_workspace(const sk_ctx &c, int64_t n) {
+    if (n <= 0) return 0;
+    const int64_t nslab = (n + kSlab - 1) / kSlab;
+    const int64_t nblk = c.pt / kBlk;
+    const int64_t ent = nslab * kSlab * c.m * (int64_t)sizeof(int2);
+    const int64_t offs = nslab * (nblk + 1) * (int64_t)sizeof(int);
+    return ((ent + 255) & ~int64_t(255)) + offs + 256;
+}
+
 cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const float *val,
-                           int64_t n, double *G, cudaStream_t s) {
+                           int64_t n, double *G, void *work, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     if (c.pt < kTileM) return cudaErrorInvalidValue;
     TcParams P;
@@ -415,31 +509,44 @@ cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const 
     if (P.N == 128 && !P.hilo) P.nstages = 6;
     if (P.N == 128 && P.hilo) P.nstages = 3;
     P.G = G;
+    P.nblk = P.pt / kBlk;
+    // workspace: bucketed entries (8 bytes each, 64 m per slab), then offsets
+    const int64_t nslab = (n + kSlab - 1) / kSlab;
+    const int64_t ent = nslab * kSlab * c.m * (int64_t)sizeof(int2);
+    unsigned char *w = static_cast<unsigned char *>(work);
+    P.bkt = reinterpret_cast<const int2 *>(w);
+    P.boff = reinterpret_cast<const int *>(w + ((ent + 255) & ~int64_t(255)));
+    bucket_kernel<<<(unsigned)nslab, 256, 0, s>>>(idx, val, n, P.m, P.pt, P.nblk,
+                                                  reinterpret_cast<int2 *>(w),
+                                                  const_cast<int *>(P.boff));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // row splits: at least enough that no segment exceeds kSegmentRows; then
-    // round the unit count up to whole waves of the SMs when that is cheap
+    // row splits: no segment longer than kSegmentRows; among the counts that
+    // allow, take the one whose units fill whole waves of the SMs best
     const int64_t min_splits = (n + kSegmentRows - 1) / kSegmentRows;
     int64_t best = min_splits;
     double best_eff = 0.0;
     for (int64_t sp = min_splits; sp <= min_splits + 64; ++sp) {
+        if ((n + sp - 1) / sp < kSlab) break;
         const int64_t units = sp * P.ntiles;
         const int64_t waves = (units + sms - 1) / sms;
         const double eff = (double)units / (double)(waves * sms);
-        if (eff > best_eff + 1e-9 && (n + sp - 1) / sp >= kSlab) {
+        if (eff > best_eff + 0.02) {
             best_eff = eff;
             best = sp;
         }
-        if (eff > 0.97) break;
+        if (eff > 0.95) break;
     }
     int64_t rps = (n + best - 1) / best;
     rps = (rps + kSlab - 1) / kSlab * kSlab;
     P.rows_per_split = rps;
     P.nsplits = (int)((n + rps - 1) / rps);
     const size_t smem = (size_t)P.nstages * P.stage_bytes + 1024 + 256;
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)P.ntiles * P.nsplits;
     gram_tc_kernel<<<(unsigned)grid, kThreads, smem, s>>>(P);

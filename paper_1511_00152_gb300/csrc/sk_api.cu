@@ -97,8 +97,15 @@ sk_status sk_precondition(const sk_ctx *ctx, const float *X, int64_t n, int64_t 
                        "sk_precondition");
 }
 
+int64_t sk_cov_workspace_bytes(const sk_ctx *ctx, int mode, int64_t n) {
+    if (!ctx || n < 0) return -1;
+    if (mode == SK_GRAM_FP32) return 0;
+    if (mode != SK_GRAM_BF16 && mode != SK_GRAM_BF16X3) return -1;
+    return sk::gram_tc_workspace(*ctx, n);
+}
+
 sk_status sk_cov_accumulate(const sk_ctx *ctx, int mode, const int32_t *idx, const float *val,
-                            int64_t n, double *G, void *stream) {
+                            int64_t n, double *G, void *work, int64_t work_bytes, void *stream) {
     SK_CHECK_CTX(ctx);
     if (n < 0) return fail(SK_EINVAL, "sk_cov_accumulate: n < 0");
     if (mode != SK_GRAM_FP32 && mode != SK_GRAM_BF16 && mode != SK_GRAM_BF16X3)
@@ -113,7 +120,13 @@ sk_status sk_cov_accumulate(const sk_ctx *ctx, int mode, const int32_t *idx, con
             return fail(SK_EUNSUPPORTED,
                         "sk_cov_accumulate: tensor-core modes need pt >= 128 (pt = %lld)",
                         (long long)ctx->pt);
-        e = sk::launch_gram_tc(*ctx, mode, idx, val, n, G, as_stream(stream));
+        const int64_t need = sk::gram_tc_workspace(*ctx, n);
+        if (!work || work_bytes < need)
+            return fail(SK_EINVAL, "sk_cov_accumulate: workspace of %lld bytes needed, %lld given",
+                        (long long)need, (long long)(work ? work_bytes : 0));
+        if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
+            return fail(SK_EINVAL, "sk_cov_accumulate: workspace must be 256-byte aligned");
+        e = sk::launch_gram_tc(*ctx, mode, idx, val, n, G, work, as_stream(stream));
     }
     return cuda_status(e, "sk_cov_accumulate");
 }

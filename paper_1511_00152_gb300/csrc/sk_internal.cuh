@@ -88,7 +88,8 @@ cudaError_t launch_kmeans_finalize(const sk_ctx &c, int K, const double *S,
 cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *val,
                              int64_t n, double *G, cudaStream_t s);
 cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx,
-                           const float *val, int64_t n, double *G, cudaStream_t s);
+                           const float *val, int64_t n, double *G, void *work, cudaStream_t s);
+int64_t gram_tc_workspace(const sk_ctx &c, int64_t n);
 cudaError_t launch_cov_finalize(const sk_ctx &c, const double *G, int64_t n_total,
                                 double *C, cudaStream_t s);
 cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out,

@@ -78,12 +78,12 @@ def initial_centres(ctx: sk.Ctx, X, rows) -> torch.Tensor:
     return sk.sk_precondition(ctx, sel)
 
 
-def covariance(ctx: sk.Ctx, idx, val, mode: int, G=None, C=None):
+def covariance(ctx: sk.Ctx, idx, val, mode: int, G=None, C=None, work=None):
     """C_n from one batch of ELL rows (Sec. V)."""
     if G is None:
         G = torch.empty((ctx.pt, ctx.pt), dtype=torch.float64, device=idx.device)
     sk.sk_cov_reset(ctx, G)
-    sk.sk_cov_accumulate(ctx, mode, idx, val, G)
+    sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=work)
     return sk.sk_cov_finalize(ctx, G, idx.shape[0], C=C)
 
 

@@ -312,7 +312,13 @@ def test_invalid_arguments_rejected_before_launch(sk):
     assert lib.sk_cov_finalize(ctx.handle, sk._ptr(G), 10, sk._ptr(G), nul) == sk.SK_EINVAL
     ctx2 = sk.sk_init(64, 4, 0)
     assert lib.sk_cov_finalize(ctx2.handle, sk._ptr(G), 10, sk._ptr(G), nul) == sk.SK_EINVAL  # overlap
-    assert lib.sk_cov_accumulate(ctx2.handle, 7, nul, nul, 5, nul, nul) == sk.SK_EINVAL
+    assert lib.sk_cov_accumulate(ctx2.handle, 7, nul, nul, 5, nul, nul, 0, nul) == sk.SK_EINVAL
+    ctx3 = sk.sk_init(256, 4, 0)
+    d = torch.zeros(16, dtype=torch.int32, device="cuda")
+    # tensor-core mode without its workspace: rejected before any launch
+    assert lib.sk_cov_accumulate(ctx3.handle, sk.SK_GRAM_BF16X3, sk._ptr(d), sk._ptr(d), 4,
+                                 sk._ptr(G), nul, 0, nul) == sk.SK_EINVAL
+    assert "workspace" in sk.sk_last_error()
     assert lib.sk_kmeans_assign(ctx2.handle, nul, nul, 5, nul, 0, nul, nul, nul) == sk.SK_EINVAL
     assert lib.sk_cov_topk(ctx2.handle, sk._ptr(G), 0, 10, nul, nul, nul, nul) == sk.SK_EINVAL
     assert "must be" in sk.sk_last_error() or sk.sk_last_error() != ""
