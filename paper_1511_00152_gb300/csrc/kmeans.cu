@@ -19,7 +19,7 @@ namespace sk {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarpsK = kThreads / 32;
 
 struct KmParams {
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     float *sS = reinterpret_cast<float *>(smem_raw + off);
     int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
     int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
-    if (PRIV && P.do_update == 1) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
+    if (PRIV && P.do_update) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
     int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + off);
 
     const int tid = threadIdx.x;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
         }
     }
-    if (PRIV && P.do_update == 1) {
+    if (PRIV && P.do_update) {
         for (int e = tid; e < KP; e += blockDim.x) {
             sS[e] = 0.f;
             sC[e] = 0;
@@ -212,18 +212,32 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                             j = __ldg(P.idx + (base + rs) * m + t) & pmask;
                             v = __ldg(P.val + (base + rs) * m + t);
                         }
-                        atomicAdd(P.S + (int64_t)newl * P.pt + j, (double)v);
-                        atomicAdd(P.cnt + (int64_t)newl * P.pt + j, 1);
-                        if ((unsigned)oldl < (unsigned)P.K) {
-                            atomicAdd(P.S + (int64_t)oldl * P.pt + j, -(double)v);
-                            atomicAdd(P.cnt + (int64_t)oldl * P.pt + j, -1);
+                        if constexpr (PRIV) {
+                            atomicAdd(sS + newl * P.pt + j, v);
+                            atomicAdd(sC + newl * P.pt + j, 1);
+                            if ((unsigned)oldl < (unsigned)P.K) {
+                                atomicAdd(sS + oldl * P.pt + j, -v);
+                                atomicAdd(sC + oldl * P.pt + j, -1);
+                            }
+                        } else {
+                            atomicAdd(P.S + (int64_t)newl * P.pt + j, (double)v);
+                            atomicAdd(P.cnt + (int64_t)newl * P.pt + j, 1);
+                            if ((unsigned)oldl < (unsigned)P.K) {
+                                atomicAdd(P.S + (int64_t)oldl * P.pt + j, -(double)v);
+                                atomicAdd(P.cnt + (int64_t)oldl * P.pt + j, -1);
+                            }
                         }
                     }
                     if (lane == 0) {
-                        atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + newl), 1ull);
-                        if ((unsigned)oldl < (unsigned)P.K)
-                            atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + oldl),
-                                      (unsigned long long)(-1LL));
+                        if constexpr (PRIV) {
+                            atomicAdd(snk + newl, 1);
+                            if ((unsigned)oldl < (unsigned)P.K) atomicAdd(snk + oldl, -1);
+                        } else {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + newl), 1ull);
+                            if ((unsigned)oldl < (unsigned)P.K)
+                                atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + oldl),
+                                          (unsigned long long)(-1LL));
+                        }
                     }
                 }
             }
@@ -269,18 +283,19 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
         }
         if constexpr (STAGE) __syncwarp();  // stage is rewritten by the next pass
     }
-    if (PRIV && P.do_update == 1) {
+    if (PRIV && P.do_update) {
         __syncthreads();
+        // a slot can carry a nonzero float sum with a zero net count (a row
+        // that left and another that joined): flush both independently
         for (int e = tid; e < KP; e += blockDim.x) {
             const int c = sC[e];
-            if (c) {
-                atomicAdd(P.S + e, (double)sS[e]);
-                atomicAdd(P.cnt + e, c);
-            }
+            const float x = sS[e];
+            if (x != 0.f) atomicAdd(P.S + e, (double)x);
+            if (c) atomicAdd(P.cnt + e, c);
         }
         for (int e = tid; e < P.K; e += blockDim.x)
             if (snk[e]) atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + e),
-                                  (unsigned long long)snk[e]);
+                                  (unsigned long long)(long long)snk[e]);
     }
 }
 
@@ -333,7 +348,7 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t mu_b = P.do_assign ? (size_t)P.pt * P.Kpad * 4 : 0;
     const size_t priv_b =
-        P.do_update == 1 ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
+        P.do_update ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
     const size_t budget = (size_t)smem_max;
     if (mu_b + priv_b <= budget) return launch_stage<KPL, true, true>(P, mu_b + priv_b, budget, s);
     if (mu_b <= budget) return launch_stage<KPL, true, false>(P, mu_b, budget, s);

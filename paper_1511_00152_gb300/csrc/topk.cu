@@ -120,60 +120,67 @@ __global__ void small_gram_kernel(const double *A, const double *B, int64_t pt, 
     if (threadIdx.x == 0) Gm[blockIdx.x] = red[0];
 }
 
-// Cholesky Gm = R^T R (upper R) and Rinv = R^{-1}, one CTA.  A pivot that is
-// not safely positive (rank-deficient block) is replaced by a tiny positive
-// value so the column is kept and re-normalised in later iterations.
-__global__ void chol_inv_kernel(const double *Gm, int b, double *Rinv) {
-    __shared__ double R[kMaxB][kMaxB + 1];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        R[e / b][e % b] = Gm[e];
+// Cholesky Gm = R^T R (upper R) and Rinv = R^{-1}, one CTA, right-looking:
+// per column c the pivot, the scaled row c, then the trailing update in
+// parallel.  A pivot that is not safely positive (rank-deficient block) is
+// replaced by a tiny positive value so the column is kept and re-normalised in
+// later iterations.
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double *Gm, int b, double *Rinv) {
+    __shared__ double A[kMaxB][kMaxB + 1];
+    __shared__ double floor_v;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < b * b; e += nt) {
+        A[e / b][e % b] = Gm[e];
         Rinv[e] = 0.0;
     }
     __syncthreads();
-    double trace = 0.0;
-    for (int c = 0; c < b; ++c) trace += R[c][c];
-    const double floor_v = 1e-300 + 1e-28 * trace;
+    if (tid == 0) {
+        double tr = 0.0;
+        for (int c = 0; c < b; ++c) tr += A[c][c];
+        floor_v = 1e-300 + 1e-28 * tr;
+    }
+    __syncthreads();
     for (int c = 0; c < b; ++c) {
         if (tid == 0) {
-            double d = R[c][c];
-            for (int q = 0; q < c; ++q) d -= R[q][c] * R[q][c];
-            R[c][c] = sqrt(d > floor_v ? d : floor_v);
+            const double d = A[c][c];
+            A[c][c] = sqrt(d > floor_v ? d : floor_v);
         }
         __syncthreads();
-        for (int j = c + 1 + tid; j < b; j += blockDim.x) {
-            double s = R[c][j];
-            for (int q = 0; q < c; ++q) s -= R[q][c] * R[q][j];
-            R[c][j] = s / R[c][c];
+        const double inv = 1.0 / A[c][c];
+        for (int j = c + 1 + tid; j < b; j += nt) A[c][j] *= inv;
+        __syncthreads();
+        const int rem = b - c - 1;
+        for (int w = tid; w < rem * rem; w += nt) {
+            const int i = c + 1 + w / rem, j = c + 1 + w % rem;
+            if (j >= i) A[i][j] -= A[c][i] * A[c][j];
         }
         __syncthreads();
     }
-    // inverse of upper-triangular R, column by column (a thread per column;
-    // each thread reads and writes only its own column of Rinv)
-    for (int j = tid; j < b; j += blockDim.x) {
+    // inverse of upper-triangular R by back substitution, a thread per column
+    // (each thread reads and writes only its own column of Rinv)
+    for (int j = tid; j < b; j += nt) {
         for (int i = j; i >= 0; --i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int q = i + 1; q <= j; ++q) s -= R[i][q] * Rinv[q * b + j];
-            Rinv[i * b + j] = s / R[i][i];
+            double sacc = (i == j) ? 1.0 : 0.0;
+            for (int q = i + 1; q <= j; ++q) sacc -= A[i][q] * Rinv[q * b + j];
+            Rinv[i * b + j] = sacc / A[i][i];
         }
     }
 }
 
-// V[c*pt + i] = sum_{q <= c} W[q*pt + i] * Rinv[q*b + c]
+// V[c*pt + i] = sum_{q <= c} W[q*pt + i] * Rinv[q*b + c], a thread per (i, c).
 __global__ void apply_rinv_kernel(const double *W, const double *Rinv, int64_t pt, int b,
                                   double *V) {
     __shared__ double Rs[kMaxB * kMaxB];
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = Rinv[e];
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double w[kMaxB];
-        for (int q = 0; q < b; ++q) w[q] = W[(int64_t)q * pt + i];
-        for (int c = 0; c < b; ++c) {
-            double s = 0.0;
-            for (int q = 0; q <= c; ++q) s = fma(w[q], Rs[q * b + c], s);
-            V[(int64_t)c * pt + i] = s;
-        }
+    const int64_t total = (int64_t)b * pt;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / pt);
+        const int64_t i = e - (int64_t)c * pt;
+        double sacc = 0.0;
+        for (int q = 0; q <= c; ++q) sacc = fma(W[(int64_t)q * pt + i], Rs[q * b + c], sacc);
+        V[e] = sacc;
     }
 }
 
@@ -383,15 +390,16 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     const dim3 pgrid((unsigned)pblocks, (unsigned)jsplit);
     int eblocks = (int)((b * pt + 255) / 256);
     if (eblocks > 4096) eblocks = 4096;
-    int ablocks = (int)((pt + 127) / 128);
+    int ablocks = (int)((b * pt + 255) / 256);
+    if (ablocks > 4096) ablocks = 4096;
     init_v_kernel<<<eblocks, 256, 0, s>>>(w.V, pt, b, k0, k1);
     for (int it = 0; it <= iters; ++it) {
         cudaMemsetAsync(w.W, 0, (size_t)b * pt * sizeof(double), s);
         panel_kernel<<<pgrid, 256, 0, s>>>(C, w.V, pt, b, jlen, w.W);
         if (it == iters) break;
         small_gram_kernel<<<b * b, 256, 0, s>>>(w.W, w.W, pt, b, w.Gm);
-        chol_inv_kernel<<<1, 64, 0, s>>>(w.Gm, b, w.Rinv);
-        apply_rinv_kernel<<<ablocks, 128, 0, s>>>(w.W, w.Rinv, pt, b, w.V);
+        chol_inv_kernel<<<1, 256, 0, s>>>(w.Gm, b, w.Rinv);
+        apply_rinv_kernel<<<ablocks, 256, 0, s>>>(w.W, w.Rinv, pt, b, w.V);
     }
     // Rayleigh-Ritz: H = V^T (C V)
     small_gram_kernel<<<b * b, 256, 0, s>>>(w.V, w.W, pt, b, w.H);
