@@ -47,11 +47,13 @@ namespace {
 
 constexpr int kProducerWarps = 8;
 constexpr int kProducers = kProducerWarps * 32;
-constexpr int kThreads = kProducers + 32;  // + the MMA warp
+constexpr int kThreads = kProducers + 64;  // + the MMA warp + the loader warp
+constexpr int kMmaWarp = kProducerWarps;
+constexpr int kLoaderWarp = kProducerWarps + 1;
+constexpr int kRing = 3;                   // bucket ranges staged ahead (slabs)
 constexpr int kSlab = 64;                  // rows per K-slab (128 bytes of BF16)
 constexpr int kTileM = 128;
 constexpr int kSegmentRows = 1 << 18;     // rows per FP32 accumulation chain (then FP64)
-constexpr int kChunk = 8;                  // bucketed entries per producer thread per pass
 constexpr int kBlk = 128;                  // column block of the bucketing
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -70,6 +72,7 @@ struct TcParams {
     int nstages;
     int stage_bytes;
     int nblk;             // pt / 128 column blocks
+    int slot_bytes;       // ring slot size (entries of one slab's A and B ranges)
     const int2 *bkt;      // bucketed entries: (block << 14 | tile byte offset, value bits)
     const int *boff;      // per slab: nblk + 1 bucket starts (relative to the slab)
     double *G;
@@ -231,9 +234,12 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     unsigned char *tiles = smem;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + (size_t)P.nstages * P.stage_bytes);
-    // bars[0..S) full, bars[S..2S) empty, bars[2S] done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * P.nstages + 1);
+    unsigned char *ring = tiles + (size_t)P.nstages * P.stage_bytes;
+    int *hdr = reinterpret_cast<int *>(ring + (size_t)kRing * P.slot_bytes);  // 8 ints per slot
+    uint64_t *bars = reinterpret_cast<uint64_t *>(hdr + 8 * kRing);
+    // bars[0..S) full, [S..2S) empty, [2S] done, [2S+1..+kRing) ring full,
+    // [2S+1+kRing..+kRing) ring empty
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * P.nstages + 1 + 2 * kRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x;
@@ -251,12 +257,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     const int S = P.nstages;
     const uint32_t a_bytes = kTileM * 128, b_bytes = (uint32_t)N * 128;
 
+    uint64_t *ring_full = bars + 2 * S + 1;
+    uint64_t *ring_empty = ring_full + kRing;
     if (tid == 0) {
-        for (int s = 0; s < 2 * S + 1; ++s) mbar_init(smem_u32(bars + s), 1);
+        for (int s = 0; s < 2 * S + 1 + 2 * kRing; ++s) mbar_init(smem_u32(bars + s), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kProducerWarps) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(256));
@@ -269,7 +277,71 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     const long long deadline = clock64() + kWaitCycles;
     const uint32_t done_bar = smem_u32(bars + 2 * S);
 
-    if (warp == kProducerWarps) {
+    if (warp == kLoaderWarp) {
+        // ---------------- loader (one thread): bucket ranges -> shared ring
+        if (lane == 0) {
+            const int R = N / kBlk;
+            const int nb1 = P.nblk + 1;
+            const int64_t slab0 = r_begin / kSlab;
+            int64_t issued = 0;
+            for (int64_t i = 0; i < nslabs; ++i) {
+                const int slot = (int)(i % kRing);
+                const uint32_t ur = (uint32_t)(i / kRing);
+                if (ur > 0 &&
+                    !mbar_wait(smem_u32(ring_empty + slot), (ur - 1) & 1u, deadline, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(&g_device_error, 1u);
+                    break;
+                }
+                const int *o = P.boff + (slab0 + i) * nb1;
+                const int a0 = __ldg(o + bi), a1 = __ldg(o + bi + 1);
+                const int b0 = __ldg(o + bj * R), b1 = __ldg(o + bj * R + R);
+                const int64_t E0 = (slab0 + i) * (int64_t)kSlab * P.m;  // slab's first entry
+                // 16-byte aligned covers of the two ranges (entries are 8 bytes)
+                const int64_t sa = (E0 + a0) & ~int64_t(1), ea = (E0 + a1 + 1) & ~int64_t(1);
+                const int64_t sb = (E0 + b0) & ~int64_t(1), eb = (E0 + b1 + 1) & ~int64_t(1);
+                const uint32_t bytesA = (uint32_t)((a1 > a0 ? ea - sa : 0) * 8);
+                const uint32_t bytesB = (uint32_t)((b1 > b0 ? eb - sb : 0) * 8);
+                int *h = hdr + 8 * slot;
+                unsigned char *dst = ring + (size_t)slot * P.slot_bytes;
+                if (bytesA + bytesB > (uint32_t)P.slot_bytes) {
+                    // does not fit: producers read this slab from global memory
+                    h[0] = a0; h[1] = a1 - a0; h[2] = b0; h[3] = b1 - b0; h[4] = 1;
+                    mbar_arrive(smem_u32(ring_full + slot));
+                } else {
+                    h[0] = (int)(E0 + a0 - sa);
+                    h[1] = a1 - a0;
+                    h[2] = (int)(bytesA / 8 + (E0 + b0 - sb));
+                    h[3] = b1 - b0;
+                    h[4] = 0;
+                    const uint32_t bar = smem_u32(ring_full + slot);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                                 "r"(bytesA + bytesB)
+                                 : "memory");
+                    if (bytesA)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                            "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+                            "l"(P.bkt + sa), "r"(bytesA), "r"(bar)
+                            : "memory");
+                    if (bytesB)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                            "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst + bytesA)),
+                            "l"(P.bkt + sb), "r"(bytesB), "r"(bar)
+                            : "memory");
+                }
+                ++issued;
+            }
+            // Before the CTA may exit, the last copy into each slot must have
+            // landed (they all have, unless the producers stopped early).
+            volatile int never = 0;
+            for (int64_t i = issued - kRing > 0 ? issued - kRing : 0; i < issued; ++i)
+                mbar_wait(smem_u32(ring_full + (i % kRing)), (uint32_t)((i / kRing) & 1),
+                          clock64() + kWaitCycles, &never);
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
             const uint32_t idesc = instr_desc(kTileM, N);
@@ -305,124 +377,69 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
         __syncwarp();
     } else {
         // ---------------- producers (then epilogue)
-        // Slab i of the segment needs bucket bi (operand A) and buckets
-        // [bj*R, bj*R + R) (operand B, R = N / 128) of the bucketed slab; both
-        // ranges are contiguous.  The ranges of slab i + 1 are known one slab
-        // ahead and its entries are loaded into registers while slab i is
-        // scattered, so the load latency overlaps the scatter and the waits.
+        // Slab i needs bucket bi (operand A) and buckets [bj*R, bj*R + R)
+        // (operand B, R = N / 128); the loader has staged both ranges in ring
+        // slot i % kRing (or flagged the slab to be read from global memory).
         const int ptid = tid;  // 0 .. kProducers-1
-        const int m = P.m;
         const int R = N / kBlk;
-        const int nb1 = P.nblk + 1;
-        const int64_t slab0 = r_begin / kSlab;  // global slab index of this segment's first slab
-        struct Ranges {
-            int a0, na, b0, nb;
-        };
-        auto ranges = [&](int64_t i) -> Ranges {
-            const int *o = P.boff + (slab0 + i) * nb1;
-            Ranges r;
-            r.a0 = __ldg(o + bi);
-            r.na = __ldg(o + bi + 1) - r.a0;
-            r.b0 = __ldg(o + bj * R);
-            r.nb = __ldg(o + bj * R + R) - r.b0;
-            return r;
-        };
-        int ck[kChunk], cv[kChunk], nk[kChunk], nv[kChunk];
-        auto load_pass = [&](int64_t i, const Ranges &r, int ps, int *kk, int *vv) {
-            const int2 *base = P.bkt + (slab0 + i) * (int64_t)kSlab * m;
-#pragma unroll
-            for (int q = 0; q < kChunk; ++q) {
-                const int e = ps * (kProducers * kChunk) + q * kProducers + ptid;
-                int2 x = make_int2(-1, 0);
-                if (e < r.na) {
-                    x = __ldg(base + r.a0 + e);
-                    x.x |= 1 << 30;  // operand A
-                } else if (e < r.na + r.nb) {
-                    x = __ldg(base + r.b0 + (e - r.na));
-                }
-                kk[q] = x.x;
-                vv[q] = x.y;
-            }
-        };
-        Ranges cur{0, 0, 0, 0}, nxt{0, 0, 0, 0};
-        if (nslabs > 0) {
-            cur = ranges(0);
-            load_pass(0, cur, 0, ck, cv);
-        }
-        if (nslabs > 1) nxt = ranges(1);
-        int64_t slab = 0;
-        int pass = 0;
+        const int64_t slab0 = r_begin / kSlab;
         bool ok = true;
-        const int per_pass = kProducers * kChunk;
-        while (slab < nslabs && ok) {
-            const int s = (int)(slab % S);
-            const uint32_t u = (uint32_t)(slab / S);
-            const int npass = (cur.na + cur.nb + per_pass - 1) / per_pass;
+        for (int64_t i = 0; i < nslabs && ok; ++i) {
+            const int s = (int)(i % S);
+            const uint32_t u = (uint32_t)(i / S);
+            const int slot = (int)(i % kRing);
+            const uint32_t ur = (uint32_t)(i / kRing);
+            bool good = true;
+            if (u > 0) good = mbar_wait(smem_u32(bars + S + s), (u - 1) & 1u, deadline, abort_flag);
+            if (good) good = mbar_wait(smem_u32(ring_full + slot), ur & 1u, deadline, abort_flag);
+            if (!good) {
+                *abort_flag = 1;
+                atomicOr(&g_device_error, 1u);
+            }
+            named_sync(1, kProducers);  // every producer sees the same abort state
+            if (*abort_flag) {
+                ok = false;
+                break;
+            }
             unsigned char *st = tiles + (size_t)s * P.stage_bytes;
-            if (pass == 0) {
-                if (u > 0) {
-                    if (!mbar_wait(smem_u32(bars + S + s), (u - 1) & 1u, deadline, abort_flag)) {
-                        *abort_flag = 1;
-                        atomicOr(&g_device_error, 1u);
-                    }
-                }
-                named_sync(1, kProducers);  // every producer sees the same abort state
-                if (*abort_flag) {
-                    ok = false;
-                    break;
-                }
-                for (int off = ptid * 16; off < P.stage_bytes; off += kProducers * 16)
-                    *reinterpret_cast<uint4 *>(st + off) = make_uint4(0u, 0u, 0u, 0u);
-                named_sync(1, kProducers);
-            }
-            const bool last_pass = pass + 1 >= npass;
-            // prefetch: the next pass of this slab, or the first pass of the next slab
-            Ranges nr = cur;
-            int64_t ns = slab;
-            int np = pass + 1;
-            if (last_pass) {
-                nr = nxt;
-                ns = slab + 1;
-                np = 0;
-            }
-            if (ns < nslabs) load_pass(ns, nr, np, nk, nv);
-            if (last_pass && slab + 2 < nslabs) nxt = ranges(slab + 2);
+            for (int off = ptid * 16; off < P.stage_bytes; off += kProducers * 16)
+                *reinterpret_cast<uint4 *>(st + off) = make_uint4(0u, 0u, 0u, 0u);
+            named_sync(1, kProducers);
             unsigned char *A_hi = st, *B_hi = st + a_bytes;
             unsigned char *A_lo = st + a_bytes + b_bytes, *B_lo = A_lo + a_bytes;
-#pragma unroll
-            for (int q = 0; q < kChunk; ++q) {
-                const int key = ck[q];
-                if (key >= 0) {
-                    const bool isA = (key >> 30) & 1;
-                    const int c = (key >> 14) & 0xFFFF;
-                    const uint32_t off = (uint32_t)(key & 16383);
-                    const float v = __int_as_float(cv[q]);
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                    const uint32_t boffb = (uint32_t)(c - bj * R) * (kBlk * 128);
-                    unsigned char *dh = isA ? A_hi + off : B_hi + boffb + off;
-                    *reinterpret_cast<__nv_bfloat16 *>(dh) = hi;
-                    if (P.hilo) {
-                        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-                        unsigned char *dl = isA ? A_lo + off : B_lo + boffb + off;
-                        *reinterpret_cast<__nv_bfloat16 *>(dl) = lo;
-                    }
+            const int *h = hdr + 8 * slot;
+            const int ha = h[0], na = h[1], hb = h[2], nb = h[3], overflow = h[4];
+            const int2 *ent = reinterpret_cast<const int2 *>(ring + (size_t)slot * P.slot_bytes);
+            const int2 *gent = P.bkt + (slab0 + i) * (int64_t)kSlab * P.m;
+            const int total = na + nb;
+            for (int e = ptid; e < total; e += kProducers) {
+                const bool isA = e < na;
+                int2 x;
+                if (!overflow) {
+                    x = isA ? ent[ha + e] : ent[hb + (e - na)];
+                } else {
+                    x = isA ? __ldg(gent + ha + e) : __ldg(gent + hb + (e - na));
+                }
+                const int c = x.x >> 14;
+                const uint32_t off = (uint32_t)(x.x & 16383);
+                const float v = __int_as_float(x.y);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                const uint32_t boffb = (uint32_t)(c - bj * R) * (kBlk * 128);
+                unsigned char *dh = isA ? A_hi + off : B_hi + boffb + off;
+                *reinterpret_cast<__nv_bfloat16 *>(dh) = hi;
+                if (P.hilo) {
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+                    unsigned char *dl = isA ? A_lo + off : B_lo + boffb + off;
+                    *reinterpret_cast<__nv_bfloat16 *>(dl) = lo;
                 }
             }
-#pragma unroll
-            for (int q = 0; q < kChunk; ++q) {
-                ck[q] = nk[q];
-                cv[q] = nv[q];
-            }
-            if (last_pass) {
-                // generic-proxy writes -> visible to the tensor core (async proxy)
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                named_sync(1, kProducers);
-                if (ptid == 0) mbar_arrive(smem_u32(bars + s));
-                ++slab;
-                pass = 0;
-                cur = nr;
-            } else {
-                ++pass;
+            // generic-proxy writes -> visible to the tensor core (async proxy);
+            // the ring slot is free once every producer is past this point
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            named_sync(1, kProducers);
+            if (ptid == 0) {
+                mbar_arrive(smem_u32(bars + s));
+                mbar_arrive(smem_u32(ring_empty + slot));
             }
         }
         // ---------------- epilogue: TMEM -> FP64 Gram
@@ -470,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == kProducerWarps) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
     }
@@ -545,7 +562,15 @@ cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const 
     rps = (rps + kSlab - 1) / kSlab * kSlab;
     P.rows_per_split = rps;
     P.nsplits = (int)((n + rps - 1) / rps);
-    const size_t smem = (size_t)P.nstages * P.stage_bytes + 1024 + 256;
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t fixed = (size_t)P.nstages * P.stage_bytes + 1024 + 512;
+    int64_t slot = ((int64_t)smem_max - (int64_t)fixed) / kRing;
+    slot = slot / 16 * 16;
+    if (slot > 65536) slot = 65536;
+    if (slot < 16) return cudaErrorInvalidConfiguration;
+    P.slot_bytes = (int)slot;
+    const size_t smem = fixed + (size_t)kRing * P.slot_bytes;
     e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)P.ntiles * P.nsplits;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     float *sS = reinterpret_cast<float *>(smem_raw + off);
     int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
     int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
-    if (PRIV && P.do_update) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
+    if (PRIV && P.do_update == 1) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
     int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + off);
 
     const int tid = threadIdx.x;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
         }
     }
-    if (PRIV && P.do_update) {
+    if (PRIV && P.do_update == 1) {
         for (int e = tid; e < KP; e += blockDim.x) {
             sS[e] = 0.f;
             sC[e] = 0;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                             j = __ldg(P.idx + (base + rs) * m + t) & pmask;
                             v = __ldg(P.val + (base + rs) * m + t);
                         }
-                        if constexpr (PRIV) {
+                        if (PRIV && P.do_update == 1) {
                             atomicAdd(sS + newl * P.pt + j, v);
                             atomicAdd(sC + newl * P.pt + j, 1);
                             if ((unsigned)oldl < (unsigned)P.K) {
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                         }
                     }
                     if (lane == 0) {
-                        if constexpr (PRIV) {
+                        if (PRIV && P.do_update == 1) {
                             atomicAdd(snk + newl, 1);
                             if ((unsigned)oldl < (unsigned)P.K) atomicAdd(snk + oldl, -1);
                         } else {
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
         }
         if constexpr (STAGE) __syncwarp();  // stage is rewritten by the next pass
     }
-    if (PRIV && P.do_update) {
+    if (PRIV && P.do_update == 1) {
         __syncthreads();
         // a slot can carry a nonzero float sum with a zero net count (a row
         // that left and another that joined): flush both independently
@@ -347,8 +347,11 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t mu_b = P.do_assign ? (size_t)P.pt * P.Kpad * 4 : 0;
+    // the incremental mode touches only rows whose label changed (few after the
+    // first passes): it adds straight into the global sums and keeps the
+    // assignment's shared-memory footprint small (room in L1 for the loads)
     const size_t priv_b =
-        P.do_update ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
+        P.do_update == 1 ? (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15) : 0;
     const size_t budget = (size_t)smem_max;
     if (mu_b + priv_b <= budget) return launch_stage<KPL, true, true>(P, mu_b + priv_b, budget, s);
     if (mu_b <= budget) return launch_stage<KPL, true, false>(P, mu_b, budget, s);
