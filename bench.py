@@ -267,7 +267,11 @@ def run_gpu(args, cfg):
         sk.sk_unmix(ctx, U, out=Ux)
         mark(4)
         sk.sk_precondition(ctx, Xsel, Y=st.mu)
-        st.graph.replay()
+        if args.no_graph:
+            for it in range(iters):
+                st.iteration(idx, val, first=(it == 0))
+        else:
+            st.graph.replay()
         mark(5)
         sk.sk_unmix(ctx, st.mu, out=cen)
         mark(6)
@@ -275,7 +279,7 @@ def run_gpu(args, cfg):
     # capture the K-means loop once (its own kernels, replayed as one graph)
     mu0 = sk.sk_precondition(ctx, Xsel)
     sk.sk_compress(ctx, X, idx=idx, val=val)
-    st.run(idx, val, mu0, iters, use_graph=True)
+    st.run(idx, val, mu0, iters, use_graph=not args.no_graph)
     torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -366,7 +370,11 @@ def run_gpu(args, cfg):
             sk.sk_unmix(ctx, U, out=Ux)
             torch.index_select(Xd2, 0, ridx, out=Xsel2)
             sk.sk_precondition(ctx, Xsel2, Y=st.mu)
-            st.graph.replay()
+            if args.no_graph:
+                for it in range(iters):
+                    st.iteration(idx, val, first=(it == 0))
+            else:
+                st.graph.replay()
             sk.sk_unmix(ctx, st.mu, out=cen)
             lab_h.copy_(st.labels, non_blocking=True)
             cen_h.copy_(cen, non_blocking=True)
@@ -435,6 +443,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=3000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the K-means loop kernel by kernel (for profilers)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
     if args.n:

@@ -111,6 +111,10 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
         const int64_t i = base + sub;
         const bool row_ok = lane_used && sub < rows_here;
         int label = 0;
+        // previous label (incremental mode), loaded before the distance loop so
+        // the load latency overlaps it
+        int old_pref = -1;
+        if (P.do_update == 2 && row_ok && kl == 0) old_pref = P.labels[i];
         if (P.do_assign) {
             uint64_t acc[NP];
 #pragma unroll
@@ -179,9 +183,8 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             bd = __shfl_sync(kFull, bd, leadl);
             bk = __shfl_sync(kFull, bk, leadl);
             label = bk;
-            int old = -1;
+            int old = old_pref;
             if (row_ok && kl == 0) {
-                if (P.do_update == 2) old = P.labels[i];
                 P.labels[i] = label;
                 if (P.dist) P.dist[i] = bd;
             }
