@@ -12,11 +12,14 @@
 //   * one thread issues tcgen05.mma kind::f16 (M = 128, N, K = 16) four times
 //     per slab (twelve for the split mode: hi*hi + hi*lo + lo*hi) into an
 //     FP32 accumulator in TMEM, and tcgen05.commit frees the stage;
-//   * after the segment, the 8 warps read the accumulator with tcgen05.ld
-//     and add it into the caller's FP64 Gram with double atomics (the FP64
-//     cross-segment reduction).
-// A segment is at most 65536 rows, which bounds the length of each FP32
-// accumulation chain.  Every mbarrier wait is bounded: on expiry the kernel
+//   * every kChunkSlabs slabs the MMAs switch to the other of two TMEM
+//     accumulators (512 columns), and the 8 producer warps read the finished
+//     one with tcgen05.ld and add it into FP32 registers with round-to-nearest
+//     adds: the tensor core's own accumulation is biased toward zero over long
+//     chains, so its chains are kept short (as in error-corrected tensor-core
+//     GEMM, Ootomo & Yokota 2022);
+//   * after the segment the registers are added into the caller's FP64 Gram
+//     with double atomics (the FP64 cross-segment reduction).  Every mbarrier wait is bounded: on expiry the kernel
 // sets the device error word, stops issuing, drains its MMAs (bounded),
 // frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -53,7 +56,8 @@ constexpr int kLoaderWarp = kProducerWarps + 1;
 constexpr int kRing = 3;                   // bucket ranges staged ahead (slabs)
 constexpr int kSlab = 64;                  // rows per K-slab (128 bytes of BF16)
 constexpr int kTileM = 128;
-constexpr int kSegmentRows = 1 << 18;     // rows per FP32 accumulation chain (then FP64)
+constexpr int kSegmentRows = 1 << 18;     // rows per work unit (FP32 registers, then FP64)
+constexpr int kChunkSlabs = 8;            // slabs per tensor-core accumulation chain
 constexpr int kBlk = 128;                  // column block of the bucketing
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -239,7 +243,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(hdr + 8 * kRing);
     // bars[0..S) full, [S..2S) empty, [2S] done, [2S+1..+kRing) ring full,
     // [2S+1+kRing..+kRing) ring empty
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * P.nstages + 1 + 2 * kRing);
+    uint64_t *acc_full = bars + 2 * P.nstages + 1 + 2 * kRing;  // [2]
+    uint64_t *acc_empty = acc_full + 2;                          // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x;
@@ -260,14 +266,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     uint64_t *ring_full = bars + 2 * S + 1;
     uint64_t *ring_empty = ring_full + kRing;
     if (tid == 0) {
-        for (int s = 0; s < 2 * S + 1 + 2 * kRing; ++s) mbar_init(smem_u32(bars + s), 1);
+        for (int s = 0; s < 2 * S + 1 + 2 * kRing + 4; ++s) mbar_init(smem_u32(bars + s), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -345,10 +351,20 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
             const uint32_t idesc = instr_desc(kTileM, N);
-            int64_t issued = 0;
             for (int64_t i = 0; i < nslabs; ++i) {
                 const int s = (int)(i % S);
                 const uint32_t u = (uint32_t)(i / S);
+                const int64_t c = i / kChunkSlabs;  // accumulation chunk
+                const int b = (int)(c & 1);
+                const bool chunk_first = (i % kChunkSlabs) == 0;
+                const bool chunk_last = (i % kChunkSlabs) == kChunkSlabs - 1 || i == nslabs - 1;
+                if (chunk_first && c >= 2 &&
+                    !mbar_wait(smem_u32(acc_empty + b), (uint32_t)(((c >> 1) - 1) & 1), deadline,
+                               abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(&g_device_error, 1u);
+                    break;
+                }
                 if (!mbar_wait(smem_u32(bars + s), u & 1u, deadline, abort_flag)) {
                     *abort_flag = 1;
                     atomicOr(&g_device_error, 1u);
@@ -358,21 +374,21 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
                 const uint32_t base = smem_u32(tiles + (size_t)s * P.stage_bytes);
                 const uint32_t a_hi = base, b_hi = base + a_bytes;
                 const uint32_t a_lo = base + a_bytes + b_bytes, b_lo = a_lo + a_bytes;
+                const uint32_t dacc = tmem + (uint32_t)(b * 256);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-                    mma_bf16(tmem, smem_desc(a_hi + kk * 32), smem_desc(b_hi + kk * 32), idesc, acc);
+                    const uint32_t acc = (!chunk_first || kk > 0) ? 1u : 0u;
+                    mma_bf16(dacc, smem_desc(a_hi + kk * 32), smem_desc(b_hi + kk * 32), idesc, acc);
                     if (P.hilo) {
-                        mma_bf16(tmem, smem_desc(a_hi + kk * 32), smem_desc(b_lo + kk * 32), idesc, 1u);
-                        mma_bf16(tmem, smem_desc(a_lo + kk * 32), smem_desc(b_hi + kk * 32), idesc, 1u);
+                        mma_bf16(dacc, smem_desc(a_hi + kk * 32), smem_desc(b_lo + kk * 32), idesc, 1u);
+                        mma_bf16(dacc, smem_desc(a_lo + kk * 32), smem_desc(b_hi + kk * 32), idesc, 1u);
                     }
                 }
                 mma_commit(smem_u32(bars + S + s));
-                ++issued;
+                if (chunk_last) mma_commit(smem_u32(acc_full + b));
             }
             // done barrier: completes when every MMA issued above has finished
             mma_commit(done_bar);
-            (void)issued;
         }
         __syncwarp();
     } else {
@@ -383,6 +399,52 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
         const int ptid = tid;  // 0 .. kProducers-1
         const int R = N / kBlk;
         const int64_t slab0 = r_begin / kSlab;
+        // FP32 round-to-nearest accumulators: warp w holds TMEM lanes
+        // 32*(w%4).. (rows of the tile) and columns 128*(w/4) .. +128
+        const int q = warp & 3, hcol = warp >> 2;
+        const bool has_cols = hcol * 128 < N;
+        float acc[128];
+#pragma unroll
+        for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+        const int64_t nchunks = (nslabs + kChunkSlabs - 1) / kChunkSlabs;
+        int64_t consumed = 0;  // chunks already added into acc
+        auto consume = [&](int64_t c) -> bool {
+            const int b = (int)(c & 1);
+            if (!mbar_wait(smem_u32(acc_full + b), (uint32_t)((c >> 1) & 1), deadline, abort_flag)) {
+                *abort_flag = 1;
+                atomicOr(&g_device_error, 1u);
+            }
+            // every producer passes the barrier, then all take the same decision
+            named_sync(1, kProducers);
+            if (*abort_flag) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (has_cols) {
+#pragma unroll
+                for (int part = 0; part < 4; ++part) {
+                    uint32_t r[32];
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) +
+                                           (uint32_t)(b * 256 + hcol * 128 + part * 32);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+                          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
+                          "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[part * 32 + j] += __uint_as_float(r[j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            named_sync(1, kProducers);
+            if (ptid == 0) mbar_arrive(smem_u32(acc_empty + b));
+            return true;
+        };
         bool ok = true;
         for (int64_t i = 0; i < nslabs && ok; ++i) {
             const int s = (int)(i % S);
@@ -441,6 +503,23 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
                 mbar_arrive(smem_u32(bars + s));
                 mbar_arrive(smem_u32(ring_empty + slot));
             }
+            // lagging one chunk behind the MMAs: add chunk c-1 into the registers
+            // while the tensor core works on chunk c
+            if ((i % kChunkSlabs) == kChunkSlabs - 1) {
+                const int64_t c = i / kChunkSlabs;
+                if (c >= 1 && consumed == c - 1) {
+                    if (!consume(c - 1)) {
+                        ok = false;
+                        break;
+                    }
+                    consumed = c;
+                }
+            }
+        }
+        // the remaining chunks
+        while (ok && consumed < nchunks) {
+            if (!consume(consumed)) break;
+            ++consumed;
         }
         // ---------------- epilogue: TMEM -> FP64 Gram
         const bool have = nslabs > 0;
@@ -457,39 +536,19 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
                 atomicOr(&g_device_error, 1u);
             }
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (have && drained && !*abort_flag) {
-            const int q = warp & 3, h = warp >> 2;
+        if (have && drained && !*abort_flag && has_cols) {
             const int row = I0 + q * 32 + lane;
-            for (int c0 = h * 128; c0 < N && c0 < h * 128 + 128; c0 += 32) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                      "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-                      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
-                      "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                double *g = P.G + (int64_t)row * P.pt + (J0 + c0);
+            double *g = P.G + (int64_t)row * P.pt + (J0 + hcol * 128);
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const float x = __uint_as_float(r[c]);
-                    if (x != 0.f) atomicAdd(g + c, (double)x);
-                }
-            }
+            for (int j = 0; j < 128; ++j)
+                if (acc[j] != 0.f) atomicAdd(g + j, (double)acc[j]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
 

@@ -143,3 +143,23 @@ def init_rows(n: int, K: int, seed: int) -> np.ndarray:
     rows go to the CUDA path and to the oracle)."""
     rng = np.random.default_rng([int(seed), 0x494E4954])
     return np.sort(rng.choice(n, size=K, replace=False)).astype(np.int64)
+
+
+def lowrank_mixture_chunk_device(n: int, p: int, seed: int, row0: int, rank: int = 50,
+                                 offsets: int = 8, noise: float = 0.1, offset_scale: float = 2.0,
+                                 device="cuda", stream=None):
+    """Rows row0 .. row0+n-1 of a stream drawn from a rank-`rank` Gaussian
+    model plus one of `offsets` mixture offsets plus N(0, noise^2) noise (the
+    streaming workload).  The loadings and offsets depend on `seed` only and
+    the rows on (seed, row0), so a chunk is the same whichever chunks come
+    before it."""
+    import torch
+    gl = _torch_gen(int(seed) * 1000003 + 17, device)
+    loadings = torch.randn(rank, p, generator=gl, device=device) / float(np.sqrt(p))
+    offs = torch.randn(offsets, p, generator=gl, device=device) * offset_scale
+    sv = torch.linspace(3.0, 0.3, rank, device=device)
+    g = _torch_gen((int(seed) * 1000003 + int(row0)) & ((1 << 62) - 1), device)
+    scores = torch.randn(n, rank, generator=g, device=device) * sv[None, :]
+    which = torch.randint(0, offsets, (n,), generator=g, device=device)
+    X = scores @ loadings + offs[which] + noise * torch.randn(n, p, generator=g, device=device)
+    return X.contiguous()
