@@ -26,6 +26,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                      argmin on tiny inputs, J' non-increasing (Sec. VI-B)
   unmix           -- D H (H D x) = x; back-map (HD)^T C_emp(Y) (HD) = C_emp(X)
   pca_topk        -- LAPACK eigh (library); compared as subspaces
+  compress_raw    -- val = x[idx] with the (pinned) mask; raw padding is zero
+  kmeans_2pass    -- brute-force dense distances and per-label means on small
+                     inputs; converged Lloyd's is a fixed point (Algorithm 2)
 """
 from __future__ import annotations
 
@@ -84,6 +87,8 @@ def _load():
             "oracle_kmeans_assign": (None, [vp, vp, i64, i64, vp, i64, i64, vp, vp]),
             "oracle_kmeans_update": (None, [vp, vp, vp, i64, i64, i64, i64, vp, vp, vp, vp]),
             "oracle_unmix": (None, [vp, i64, i64, i64, u64, vp]),
+            "oracle_compress_raw": (None, [vp, i64, i64, i64, i64, i64, u64, vp, vp]),
+            "oracle_kmeans_2pass": (None, [vp, i64, i64, vp, vp, i64, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -171,6 +176,16 @@ def compress(X, m: int, seed: int, row0: int = 0):
     idx = np.zeros((n, m), np.int32)
     val = np.zeros((n, m), np.float64)
     _load().oracle_compress(_p(X), n, p, p, row0, m, seed, _p(idx), _p(val))
+    return idx, val
+
+
+def compress_raw(X, m: int, seed: int, row0: int = 0):
+    """Ablation without preconditioning (H = D = I): ELL of the padded raw rows."""
+    X = _c(X, np.float32)
+    n, p = X.shape
+    idx = np.zeros((n, m), np.int32)
+    val = np.zeros((n, m), np.float64)
+    _load().oracle_compress_raw(_p(X), n, p, p, row0, m, seed, _p(idx), _p(val))
     return idx, val
 
 
@@ -272,6 +287,21 @@ def kmeans(idx, val, mu0, pt: int, iters: int):
         history.append(kmeans_objective(idx, val, labels, mu))
         mu, _counts, _nk = kmeans_update(idx, val, labels, mu, pt)
     return labels, mu, history
+
+
+def kmeans_2pass(X, labels1, mu1):
+    """Algorithm 2's second pass: (labels2, mu2, counts) from the raw rows, the
+    1-pass labels and the 1-pass (un-mixed) centres."""
+    X = _c(X, np.float32)
+    n, p = X.shape
+    c1 = _c(labels1, np.int32)
+    mu1 = _c(mu1, np.float64)
+    K = mu1.shape[0]
+    c2 = np.zeros(n, np.int32)
+    mu2 = np.zeros((K, p), np.float64)
+    counts = np.zeros(K, np.int64)
+    _load().oracle_kmeans_2pass(_p(X), n, p, _p(c1), _p(mu1), K, _p(c2), _p(mu2), _p(counts))
+    return c2, mu2, counts
 
 
 def unmix(M, p: int, seed: int) -> np.ndarray:

@@ -189,6 +189,21 @@ void oracle_precondition(const float *X, int64_t n, int64_t p, int64_t ldx,
     free(D);
 }
 
+/* Ablation without preconditioning (H = D = I, the "no preconditioning"
+ * variant of Sec. VII): the mask of row r over [0, pt) of the zero-padded x,
+ * val = x[idx].  Same mask stream as oracle_compress. */
+void oracle_compress_raw(const float *X, int64_t n, int64_t p, int64_t ldx, int64_t row0,
+                         int64_t m, uint64_t seed, int32_t *idx, double *val) {
+    int64_t pt = oracle_ptilde(p);
+    for (int64_t i = 0; i < n; ++i) {
+        oracle_mask(pt, m, seed, row0 + i, idx + i * m);
+        for (int64_t t = 0; t < m; ++t) {
+            int64_t j = idx[i * m + t];
+            val[i * m + t] = (j < p) ? (double)X[i * ldx + j] : 0.0;
+        }
+    }
+}
+
 /* Compression of rows row0..row0+n-1: w_i = R_i R_i^T y_i stored as ELL
  * (idx[i][t] = Omega_r[t], val[i][t] = y_i[Omega_r[t]]), Algorithm 1. */
 void oracle_compress(const float *X, int64_t n, int64_t p, int64_t ldx, int64_t row0,
@@ -304,4 +319,37 @@ void oracle_unmix(const double *in, int64_t r, int64_t pt, int64_t p, uint64_t s
     }
     free(D);
     free(y);
+}
+
+/* Second pass of the 2-pass sparsified K-means (Algorithm 2): with the 1-pass
+ * labels c1 and the 1-pass centres mu1 (data domain, K x p), every raw row is
+ * assigned to its nearest mu1 (dense squared distance, ties to the smallest
+ * k) and added to the mean of its 1-pass cluster.  mu2 = sum / |I_k|; a
+ * cluster with no 1-pass row keeps mu1 (the algorithm does not define it). */
+void oracle_kmeans_2pass(const float *X, int64_t n, int64_t p, const int32_t *c1,
+                         const double *mu1, int64_t K, int32_t *c2, double *mu2,
+                         int64_t *counts) {
+    double *sum = (double *)calloc((size_t)(K * p), sizeof(double));
+    for (int64_t k = 0; k < K; ++k) counts[k] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float *x = X + i * p;
+        int64_t k1 = c1[i];
+        counts[k1] += 1;
+        for (int64_t j = 0; j < p; ++j) sum[k1 * p + j] += (double)x[j];
+        int64_t best = 0;
+        double bestd = INFINITY;
+        for (int64_t k = 0; k < K; ++k) {
+            double d = 0.0;
+            for (int64_t j = 0; j < p; ++j) {
+                double diff = (double)x[j] - mu1[k * p + j];
+                d += diff * diff;
+            }
+            if (d < bestd) { bestd = d; best = k; }
+        }
+        c2[i] = (int32_t)best;
+    }
+    for (int64_t k = 0; k < K; ++k)
+        for (int64_t j = 0; j < p; ++j)
+            mu2[k * p + j] = counts[k] > 0 ? sum[k * p + j] / (double)counts[k] : mu1[k * p + j];
+    free(sum);
 }

@@ -94,3 +94,53 @@ def test_objective_non_increasing_tiny_config():
     # J' after each update is <= J' before it; the history records J' at each
     # assignment, which can only go down
     assert all(b <= a * (1 + 1e-12) for a, b in zip(hist, hist[1:]))
+
+
+def test_2pass_brute_force_and_uses_1pass_labels():
+    """Algorithm 2: means under the 1-pass labels, labels against the 1-pass centres."""
+    rng = np.random.default_rng(8)
+    n, p, K = 60, 12, 4
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    c1 = rng.integers(0, K - 1, n).astype(np.int32)  # cluster K-1 empty in pass 1
+    mu1 = rng.standard_normal((K, p))
+    c2, mu2, counts = oracle.kmeans_2pass(X, c1, mu1)
+    Xd = X.astype(np.float64)
+    d = ((Xd[:, None, :] - mu1[None]) ** 2).sum(-1)
+    assert np.array_equal(c2, np.argmin(d, axis=1))
+    for k in range(K):
+        sel = c1 == k
+        assert counts[k] == sel.sum()
+        if sel.any():
+            assert np.allclose(mu2[k], Xd[sel].mean(0), rtol=1e-14, atol=1e-14)
+        else:
+            assert np.array_equal(mu2[k], mu1[k])
+    # the means follow the 1-pass labels, not the new ones
+    assert not np.array_equal(c1, c2)
+
+
+def test_2pass_fixed_point_of_converged_lloyd():
+    """With m = p the 1-pass method is Lloyd's; at its fixed point the extra
+    pass changes neither labels nor centres."""
+    n, p, K, seed = 400, 16, 3, 4
+    X, _, _ = synth.mixture(n, p, K, seed=6, heavy_frac=0.0)
+    pt = oracle.ptilde(p)
+    idx, val = oracle.compress(X, pt, seed)
+    rows = oracle.init_rows(n, K, seed)
+    Y = oracle.precondition(X, seed)
+    labels, mu, _ = oracle.kmeans(idx, val, Y[rows], pt, iters=30)
+    # one more assign with the final centres gives the labels the centres came from
+    labels, _ = oracle.kmeans_assign(idx, val, mu, pt)
+    mu_x = oracle.unmix(mu, p, seed)
+    c2, mu2, _ = oracle.kmeans_2pass(X, labels, mu_x)
+    assert np.array_equal(c2, labels)
+    assert np.max(np.abs(mu2 - mu_x)) < 1e-10
+
+
+def test_compress_raw_is_gather_of_padded_rows():
+    X = synth.uniform(20, 50, seed=2)
+    idx, val = oracle.compress_raw(X, 9, 3, row0=77)
+    Xp = np.zeros((20, 64))
+    Xp[:, :50] = X
+    for i in range(20):
+        assert np.array_equal(idx[i], oracle.mask(64, 9, 3, 77 + i))
+        assert np.array_equal(val[i], Xp[i, idx[i]])
