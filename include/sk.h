@@ -59,7 +59,17 @@ enum {
     SK_GRAM_BF16X3 = 2  /* split-BF16 hi/lo, three tcgen05 products */
 };
 
-/* Opaque host-side handle: p, pt, m and the seed.  Holds no device memory. */
+/* Flags for sk_init_ex. */
+enum {
+    /* Ablation without preconditioning (H = D = I; the "no preconditioning"
+     * comparison of Sec. VII): sk_compress samples the zero-padded raw row,
+     * val = [x_i; 0][Omega], sk_precondition pads only, and sk_unmix /
+     * sk_unmix_f64 truncate to p.  Estimators and K-means are unchanged. */
+    SK_FLAG_NO_PRECONDITION = 1
+};
+
+/* Opaque host-side handle: p, pt, m, the seed and the flags.  Holds no
+ * device memory. */
 typedef struct sk_ctx sk_ctx;
 
 /* Creates a handle for samples of dimension p keeping m of pt entries per
@@ -68,6 +78,13 @@ typedef struct sk_ctx sk_ctx;
  * and 1 <= m <= pt.  *ctx receives the handle (host memory, freed by
  * sk_destroy).  Returns SK_EINVAL / SK_EUNSUPPORTED / SK_ENOMEM. */
 sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed);
+
+/* sk_init with flags (a bitwise OR of SK_FLAG_*; 0 is sk_init).  Unknown
+ * bits return SK_EINVAL. */
+sk_status sk_init_ex(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed, uint32_t flags);
+
+/* The flags of a handle (0 for NULL). */
+uint32_t sk_flags(const sk_ctx *ctx);
 
 /* Frees a handle from sk_init (NULL is ignored). */
 void sk_destroy(sk_ctx *ctx);
@@ -216,6 +233,45 @@ sk_status sk_unmix(const sk_ctx *ctx, const float *in, int64_t r, float *out,
 /* float64 variant of sk_unmix (for eigenvectors): in r x pt, out r x p. */
 sk_status sk_unmix_f64(const sk_ctx *ctx, const double *in, int64_t r, double *out,
                        void *stream);
+
+/* Second pass of the 2-pass sparsified K-means (Algorithm 2), first half:
+ * for each raw row x_i (X: device n x p float32, leading dimension ldx >= p),
+ * labels[i] = argmin_k ||x_i - mu[k]||^2 over all p coordinates, ties to the
+ * smallest k, the squared distance formed directly in float32 (no norm
+ * expansion).  mu: device K x p float32, the un-mixed 1-pass centres.
+ * labels: device int32 n; dist: device float32 n or NULL.  1 <= K <= 256.
+ * Pass 2 reads X once; it may be called on row chunks. */
+sk_status sk_kmeans2_assign(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                            const float *mu, int32_t K, int32_t *labels, float *dist,
+                            void *stream);
+
+/* Second pass of Algorithm 2, second half: the cluster means of the raw rows
+ * under the *1-pass* labels (labels1: device int32 n, each in [0, K)):
+ * sums[k*p + j] += sum of X[i, j] over rows with labels1[i] = k (device
+ * float64 K x p) and counts[k] += rows in cluster k (device int64 K), both
+ * caller-zeroed before the first chunk.  Rows with a label outside [0, K)
+ * are skipped. */
+sk_status sk_kmeans2_sums(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                          const int32_t *labels1, int32_t K, double *sums, int64_t *counts,
+                          void *stream);
+
+/* Algorithm 2's centres: mu[k*p + j] = sums/counts[k] (device float32 K x p,
+ * in place) where counts[k] > 0; a cluster with no 1-pass row keeps its
+ * 1-pass centre. */
+sk_status sk_kmeans2_finalize(const sk_ctx *ctx, int32_t K, const double *sums,
+                              const int64_t *counts, float *mu, void *stream);
+
+/* Sample-mean estimator (Sec. IV), accumulation: sums[j] += sum over the n
+ * ELL rows of the values sampled at coordinate j, i.e. sum_i R_i R_i^T y_i.
+ * sums: device float64 pt, caller-zeroed before the first chunk. */
+sk_status sk_mean_accumulate(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                             int64_t n, double *sums, void *stream);
+
+/* Sample-mean estimator (Sec. IV): mean = (pt/m) (1/n_total) sums (device
+ * float64 pt, preconditioned domain; sk_unmix_f64 maps it back to the data
+ * domain).  n_total >= 1.  sums and mean may be the same buffer. */
+sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_total,
+                           double *mean, void *stream);
 
 /* Reports SK_ETIMEOUT if a bounded device wait of this library ran out since
  * the last call (and clears the flag), SK_ECUDA on a pending CUDA error, else

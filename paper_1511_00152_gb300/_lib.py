@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sk.h")
 
 SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = range(6)
 SK_GRAM_FP32, SK_GRAM_BF16, SK_GRAM_BF16X3 = 0, 1, 2
+SK_FLAG_NO_PRECONDITION = 1
 STATUS_NAMES = {0: "SK_OK", 1: "SK_EINVAL", 2: "SK_ENOMEM", 3: "SK_ECUDA",
                 4: "SK_ETIMEOUT", 5: "SK_EUNSUPPORTED"}
 
@@ -48,6 +49,8 @@ def load(path: str | None = None):
         st = ctypes.c_int
         sigs = {
             "sk_init": (st, [ctypes.POINTER(vp), i64, i64, u64]),
+            "sk_init_ex": (st, [ctypes.POINTER(vp), i64, i64, u64, ctypes.c_uint32]),
+            "sk_flags": (ctypes.c_uint32, [vp]),
             "sk_destroy": (None, [vp]),
             "sk_ptilde": (i64, [vp]),
             "sk_compress": (st, [vp, vp, i64, i64, i64, vp, vp, vp]),
@@ -67,6 +70,11 @@ def load(path: str | None = None):
             "sk_kmeans_finalize": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_unmix": (st, [vp, vp, i64, vp, vp]),
             "sk_unmix_f64": (st, [vp, vp, i64, vp, vp]),
+            "sk_kmeans2_assign": (st, [vp, vp, i64, i64, vp, i32, vp, vp, vp]),
+            "sk_kmeans2_sums": (st, [vp, vp, i64, i64, vp, i32, vp, vp, vp]),
+            "sk_kmeans2_finalize": (st, [vp, i32, vp, vp, vp, vp]),
+            "sk_mean_accumulate": (st, [vp, vp, vp, i64, vp, vp]),
+            "sk_mean_finalize": (st, [vp, vp, i64, vp, vp]),
             "sk_device_status": (st, [vp]),
             "sk_last_error": (ctypes.c_char_p, []),
         }
@@ -120,6 +128,7 @@ class Ctx:
         self._h = ctypes.c_void_p(handle)
         self.p, self.m, self.seed = p, m, seed
         self.pt = int(load().sk_ptilde(self._h))
+        self.flags = int(load().sk_flags(self._h))
 
     @property
     def handle(self):
@@ -138,6 +147,17 @@ def sk_init(p: int, m: int, seed: int) -> Ctx:
     h = ctypes.c_void_p(0)
     _check("sk_init", load().sk_init(ctypes.byref(h), int(p), int(m), int(seed) & (2**64 - 1)))
     return Ctx(h.value, int(p), int(m), int(seed))
+
+
+def sk_init_ex(p: int, m: int, seed: int, flags: int) -> Ctx:
+    h = ctypes.c_void_p(0)
+    _check("sk_init_ex", load().sk_init_ex(ctypes.byref(h), int(p), int(m),
+                                           int(seed) & (2**64 - 1), int(flags)))
+    return Ctx(h.value, int(p), int(m), int(seed))
+
+
+def sk_flags(ctx: Ctx) -> int:
+    return int(load().sk_flags(ctx.handle))
 
 
 def sk_ptilde(ctx: Ctx) -> int:
@@ -307,6 +327,65 @@ def sk_unmix(ctx: Ctx, M, out=None, stream=None):
         out = torch.empty((r, ctx.p), dtype=torch.float32, device=M.device)
     _check("sk_unmix", load().sk_unmix(ctx.handle, _ptr(M), r, _ptr(out), _stream(stream)))
     return out
+
+
+def sk_kmeans2_assign(ctx: Ctx, X, mu, labels=None, dist=None, stream=None):
+    """Algorithm 2: labels of the raw rows against the un-mixed centres mu (K x p)."""
+    n, ldx = _rows_ld(X, ctx.p)
+    K = mu.shape[0]
+    _need(mu, torch.float32, "mu", (K, ctx.p))
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    _need(labels, torch.int32, "labels", (n,))
+    if dist is not None:
+        _need(dist, torch.float32, "dist", (n,))
+    _check("sk_kmeans2_assign", load().sk_kmeans2_assign(ctx.handle, _ptr(X), n, ldx, _ptr(mu),
+                                                         K, _ptr(labels), _ptr(dist),
+                                                         _stream(stream)))
+    return labels, dist
+
+
+def sk_kmeans2_sums(ctx: Ctx, X, labels1, K: int, sums, counts, stream=None):
+    """Algorithm 2: sums (K x p float64) and counts (K int64) under the 1-pass labels."""
+    n, ldx = _rows_ld(X, ctx.p)
+    _need(labels1, torch.int32, "labels1", (n,))
+    _need(sums, torch.float64, "sums", (K, ctx.p))
+    _need(counts, torch.int64, "counts", (K,))
+    _check("sk_kmeans2_sums", load().sk_kmeans2_sums(ctx.handle, _ptr(X), n, ldx, _ptr(labels1),
+                                                     int(K), _ptr(sums), _ptr(counts),
+                                                     _stream(stream)))
+    return sums, counts
+
+
+def sk_kmeans2_finalize(ctx: Ctx, sums, counts, mu, stream=None):
+    K = mu.shape[0]
+    _need(mu, torch.float32, "mu", (K, ctx.p))
+    _need(sums, torch.float64, "sums", (K, ctx.p))
+    _need(counts, torch.int64, "counts", (K,))
+    _check("sk_kmeans2_finalize", load().sk_kmeans2_finalize(ctx.handle, K, _ptr(sums),
+                                                             _ptr(counts), _ptr(mu),
+                                                             _stream(stream)))
+    return mu
+
+
+def sk_mean_accumulate(ctx: Ctx, idx, val, sums, stream=None):
+    n = idx.shape[0]
+    _need(idx, torch.int32, "idx", (n, ctx.m))
+    _need(val, torch.float32, "val", (n, ctx.m))
+    _need(sums, torch.float64, "sums", (ctx.pt,))
+    _check("sk_mean_accumulate", load().sk_mean_accumulate(ctx.handle, _ptr(idx), _ptr(val), n,
+                                                           _ptr(sums), _stream(stream)))
+    return sums
+
+
+def sk_mean_finalize(ctx: Ctx, sums, n_total: int, mean=None, stream=None):
+    _need(sums, torch.float64, "sums", (ctx.pt,))
+    if mean is None:
+        mean = torch.empty_like(sums)
+    _need(mean, torch.float64, "mean", (ctx.pt,))
+    _check("sk_mean_finalize", load().sk_mean_finalize(ctx.handle, _ptr(sums), int(n_total),
+                                                       _ptr(mean), _stream(stream)))
+    return mean
 
 
 def sk_device_status(stream=None) -> int:

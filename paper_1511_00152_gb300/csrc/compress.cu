@@ -36,6 +36,7 @@ struct CompressParams {
     float *Y;
     float scale;
     int vec;
+    int mix;            // 0: no preconditioning (H = D = I), the ablation of Sec. VII
     unsigned int *err;  // device error word (bounded waits)
 };
 
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
     // Sign bits of the 32 coordinates this thread holds in phase A.
     uint32_t smask = 0;
 #pragma unroll 1
-    for (int r = 0; r < 32; ++r) {
+    for (int r = 0; r < (P.mix ? 32 : 0); ++r) {
         const int e = 128 * (r >> 2) + 4 * lane + (r & 3);
         const int c = (L <= 10) ? (e & (PT - 1)) : (1024 * wg + e);
         smask |= sign_bit(P.k0, P.k1, (uint32_t)c) << r;
@@ -396,10 +397,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
             w2[P2] = ((uint64_t)b << 32) | a;
         }
         // ---- phase A: register bit rb <-> element bit {0,1,7,8,9}[rb]
+        if (P.mix) {
 #pragma unroll
-        for (int rb = 0; rb < 5; ++rb) {
-            const int eb = rb < 2 ? rb : rb + 5;
-            if (eb < L) wht_stage<16>(w2, rb);
+            for (int rb = 0; rb < 5; ++rb) {
+                const int eb = rb < 2 ? rb : rb + 5;
+                if (eb < L) wht_stage<16>(w2, rb);
+            }
         }
         // every lane has read its samples (TMA) / previous gathers are done
         group_sync<G>(grp);
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
         }
         __syncwarp();
         // ---- phase B: lane = (q, i''), register j <-> element bits 2..6
-        {
+        if (P.mix) {
             const int q = lane & 3, ib = lane >> 2;
 #pragma unroll
             for (int P2 = 0; P2 < 16; ++P2)
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
             }
         }
         // ---- phase C (pt > 1024): element bits 10.. across the group's warps
-        if constexpr (L > 10) {
+        if (L > 10 && P.mix) {
             constexpr int S = 32 / G;
             group_sync<G>(grp);
             const int tau = wg * 32 + lane;
@@ -558,7 +561,8 @@ cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t 
     P.idx = idx;
     P.val = val;
     P.Y = Y;
-    P.scale = (float)(1.0 / sqrt((double)c.pt));
+    P.mix = (c.flags & SK_FLAG_NO_PRECONDITION) ? 0 : 1;
+    P.scale = P.mix ? (float)(1.0 / sqrt((double)c.pt)) : 1.0f;
     P.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (c.p % 4 == 0) && (ldx % 4 == 0);
     P.err = device_error_word();
     if (n == 0) return cudaSuccess;

@@ -46,6 +46,12 @@ bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
 extern "C" {
 
 sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed) {
+    return sk_init_ex(ctx, p, m, seed, 0u);
+}
+
+uint32_t sk_flags(const sk_ctx *ctx) { return ctx ? ctx->flags : 0u; }
+
+sk_status sk_init_ex(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed, uint32_t flags) {
     if (!ctx) return fail(SK_EINVAL, "sk_init: ctx out-pointer is NULL");
     *ctx = nullptr;
     if (p < 1) return fail(SK_EINVAL, "sk_init: p = %lld must be >= 1", (long long)p);
@@ -56,6 +62,8 @@ sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed) {
     if (m < 1 || m > pt)
         return fail(SK_EINVAL, "sk_init: m = %lld must be in [1, pt = %lld]", (long long)m,
                     (long long)pt);
+    if (flags & ~(uint32_t)SK_FLAG_NO_PRECONDITION)
+        return fail(SK_EINVAL, "sk_init: unknown flag bits 0x%x", flags);
     sk_ctx *c = new (std::nothrow) sk_ctx;
     if (!c) return fail(SK_ENOMEM, "sk_init: out of host memory");
     c->p = p;
@@ -63,6 +71,7 @@ sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed) {
     c->log2pt = L;
     c->m = m;
     c->seed = seed;
+    c->flags = flags;
     *ctx = c;
     g_msg[0] = 0;
     return SK_OK;
@@ -292,6 +301,63 @@ sk_status sk_unmix_f64(const sk_ctx *ctx, const double *in, int64_t r, double *o
         return fail(SK_EINVAL, "sk_unmix_f64: in and out overlap");
     return cuda_status(sk::launch_unmix(*ctx, in, r, out, true, as_stream(stream)),
                        "sk_unmix_f64");
+}
+
+sk_status sk_kmeans2_assign(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                            const float *mu, int32_t K, int32_t *labels, float *dist,
+                            void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 0) return fail(SK_EINVAL, "sk_kmeans2_assign: n < 0");
+    if (ldx < ctx->p) return fail(SK_EINVAL, "sk_kmeans2_assign: ldx < p");
+    if (K < 1 || K > 256) return fail(SK_EINVAL, "sk_kmeans2_assign: K = %d must be in [1, 256]", K);
+    if (n == 0) return SK_OK;
+    if (!X || !mu || !labels) return fail(SK_EINVAL, "sk_kmeans2_assign: NULL buffer");
+    return cuda_status(sk::launch_kmeans2_assign(*ctx, X, n, ldx, mu, K, labels, dist,
+                                                 as_stream(stream)),
+                       "sk_kmeans2_assign");
+}
+
+sk_status sk_kmeans2_sums(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                          const int32_t *labels1, int32_t K, double *sums, int64_t *counts,
+                          void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 0) return fail(SK_EINVAL, "sk_kmeans2_sums: n < 0");
+    if (ldx < ctx->p) return fail(SK_EINVAL, "sk_kmeans2_sums: ldx < p");
+    if (K < 1 || K > 256) return fail(SK_EINVAL, "sk_kmeans2_sums: K = %d must be in [1, 256]", K);
+    if (n == 0) return SK_OK;
+    if (!X || !labels1 || !sums || !counts) return fail(SK_EINVAL, "sk_kmeans2_sums: NULL buffer");
+    if (n > ((int64_t)1 << 40)) return fail(SK_EUNSUPPORTED, "sk_kmeans2_sums: n too large");
+    return cuda_status(sk::launch_kmeans2_sums(*ctx, X, n, ldx, labels1, K, sums, counts,
+                                               as_stream(stream)),
+                       "sk_kmeans2_sums");
+}
+
+sk_status sk_kmeans2_finalize(const sk_ctx *ctx, int32_t K, const double *sums,
+                              const int64_t *counts, float *mu, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (K < 1 || K > 256) return fail(SK_EINVAL, "sk_kmeans2_finalize: K out of range");
+    if (!sums || !counts || !mu) return fail(SK_EINVAL, "sk_kmeans2_finalize: NULL buffer");
+    return cuda_status(sk::launch_kmeans2_finalize(*ctx, K, sums, counts, mu, as_stream(stream)),
+                       "sk_kmeans2_finalize");
+}
+
+sk_status sk_mean_accumulate(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                             int64_t n, double *sums, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 0) return fail(SK_EINVAL, "sk_mean_accumulate: n < 0");
+    if (n == 0) return SK_OK;
+    if (!idx || !val || !sums) return fail(SK_EINVAL, "sk_mean_accumulate: NULL buffer");
+    return cuda_status(sk::launch_mean_accumulate(*ctx, idx, val, n, sums, as_stream(stream)),
+                       "sk_mean_accumulate");
+}
+
+sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_total, double *mean,
+                           void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n_total < 1) return fail(SK_EINVAL, "sk_mean_finalize: n_total < 1");
+    if (!sums || !mean) return fail(SK_EINVAL, "sk_mean_finalize: NULL buffer");
+    return cuda_status(sk::launch_mean_finalize(*ctx, sums, n_total, mean, as_stream(stream)),
+                       "sk_mean_finalize");
 }
 
 sk_status sk_device_status(void *stream) {

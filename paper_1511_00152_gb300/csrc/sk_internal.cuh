@@ -73,6 +73,7 @@ struct sk_ctx {
     int log2pt;
     int64_t m;
     uint64_t seed;
+    uint32_t flags;  // SK_FLAG_* of sk_init_ex
 };
 
 namespace sk {
@@ -94,6 +95,19 @@ cudaError_t launch_cov_finalize(const sk_ctx &c, const double *G, int64_t n_tota
                                 double *C, cudaStream_t s);
 cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out,
                          bool f64, cudaStream_t s);
+// Algorithm 2's second pass and the sample mean (extras.cu).
+cudaError_t launch_kmeans2_assign(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                                  const float *mu, int K, int32_t *labels, float *dist,
+                                  cudaStream_t s);
+cudaError_t launch_kmeans2_sums(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                                const int32_t *labels, int K, double *sums, int64_t *counts,
+                                cudaStream_t s);
+cudaError_t launch_kmeans2_finalize(const sk_ctx &c, int K, const double *sums,
+                                    const int64_t *counts, float *mu, cudaStream_t s);
+cudaError_t launch_mean_accumulate(const sk_ctx &c, const int32_t *idx, const float *val,
+                                   int64_t n, double *sums, cudaStream_t s);
+cudaError_t launch_mean_finalize(const sk_ctx &c, const double *sums, int64_t n_total,
+                                 double *mean, cudaStream_t s);
 cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters,
                         double *evals, double *U, double *work, cudaStream_t s);
 int64_t topk_workspace(int64_t pt, int k);

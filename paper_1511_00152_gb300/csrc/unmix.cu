@@ -10,13 +10,13 @@ namespace {
 
 template <typename T>
 __global__ void unmix_kernel(const T *in, int64_t r, int pt, int p, uint32_t k0,
-                             uint32_t k1, T scale, T *out) {
+                             uint32_t k1, T scale, int mix, T *out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *y = reinterpret_cast<T *>(smem_raw);
     for (int64_t row = blockIdx.x; row < r; row += gridDim.x) {
         for (int j = threadIdx.x; j < pt; j += blockDim.x) y[j] = in[row * pt + j];
         __syncthreads();
-        for (int h = 1; h < pt; h <<= 1) {
+        for (int h = 1; h < (mix ? pt : 1); h <<= 1) {
             for (int q = threadIdx.x; q < pt / 2; q += blockDim.x) {
                 const int lo = (q / h) * 2 * h + (q % h);
                 const T a = y[lo], b = y[lo + h];
@@ -27,7 +27,7 @@ __global__ void unmix_kernel(const T *in, int64_t r, int pt, int p, uint32_t k0,
         }
         for (int j = threadIdx.x; j < p; j += blockDim.x) {
             const T v = y[j] * scale;
-            out[row * p + j] = sign_bit(k0, k1, (uint32_t)j) ? -v : v;
+            out[row * p + j] = (mix && sign_bit(k0, k1, (uint32_t)j)) ? -v : v;
         }
         __syncthreads();
     }
@@ -41,19 +41,21 @@ cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out, 
     const int threads = c.pt >= 512 ? 512 : (c.pt >= 32 ? (int)c.pt : 32);
     int blocks = (int)(r < 1024 ? r : 1024);
     const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
-    const double sc = 1.0 / sqrt((double)c.pt);
+    // without preconditioning (H = D = I) un-mixing is the truncation to p
+    const int mix = (c.flags & SK_FLAG_NO_PRECONDITION) ? 0 : 1;
+    const double sc = mix ? 1.0 / sqrt((double)c.pt) : 1.0;
     if (f64) {
         const size_t smem = (size_t)c.pt * 8;
         cudaError_t e = cudaFuncSetAttribute(unmix_kernel<double>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         unmix_kernel<double><<<blocks, threads, smem, s>>>(
-            static_cast<const double *>(in), r, (int)c.pt, (int)c.p, k0, k1, sc,
+            static_cast<const double *>(in), r, (int)c.pt, (int)c.p, k0, k1, sc, mix,
             static_cast<double *>(out));
     } else {
         const size_t smem = (size_t)c.pt * 4;
         unmix_kernel<float><<<blocks, threads, smem, s>>>(
-            static_cast<const float *>(in), r, (int)c.pt, (int)c.p, k0, k1, (float)sc,
+            static_cast<const float *>(in), r, (int)c.pt, (int)c.p, k0, k1, (float)sc, mix,
             static_cast<float *>(out));
     }
     return cudaGetLastError();

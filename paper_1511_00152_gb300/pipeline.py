@@ -72,6 +72,35 @@ class KMeansState:
         return self.labels, self.mu
 
 
+def kmeans_2pass(ctx: sk.Ctx, X, labels1, mu_x, chunk_rows: int | None = None):
+    """Second pass of Algorithm 2 over the raw rows X (n x p): labels against
+    the un-mixed 1-pass centres mu_x (K x p) and the means of X under the
+    1-pass labels.  Returns (labels2, mu2 [K x p], counts [K]).  With
+    chunk_rows the pass streams X in row chunks (out-of-core input)."""
+    n = X.shape[0]
+    K = mu_x.shape[0]
+    labels2 = torch.empty(n, dtype=torch.int32, device=X.device)
+    sums = torch.zeros((K, ctx.p), dtype=torch.float64, device=X.device)
+    counts = torch.zeros(K, dtype=torch.int64, device=X.device)
+    step = chunk_rows or max(n, 1)
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        sk.sk_kmeans2_assign(ctx, X[a:b], mu_x, labels=labels2[a:b])
+        sk.sk_kmeans2_sums(ctx, X[a:b], labels1[a:b], K, sums, counts)
+    mu2 = sk.sk_kmeans2_finalize(ctx, sums, counts, mu_x.clone())
+    return labels2, mu2, counts
+
+
+def sample_mean(ctx: sk.Ctx, idx, val, n_total: int | None = None, sums=None):
+    """Sample-mean estimator (Sec. IV) of the ELL rows: (mean in the
+    preconditioned domain [pt], mean un-mixed to the data domain [p])."""
+    if sums is None:
+        sums = torch.zeros(ctx.pt, dtype=torch.float64, device=idx.device)
+        sk.sk_mean_accumulate(ctx, idx, val, sums)
+    mean = sk.sk_mean_finalize(ctx, sums, n_total or idx.shape[0])
+    return mean, sk.sk_unmix(ctx, mean[None, :])[0]
+
+
 def initial_centres(ctx: sk.Ctx, X, rows) -> torch.Tensor:
     """Preconditioned rows X[rows] (dense y = H D x) as starting centres."""
     sel = X[torch.as_tensor(rows, device=X.device, dtype=torch.long)].contiguous()

@@ -43,3 +43,13 @@ def test_host_validation_without_gpu():
     assert lib.sk_cov_topk_workspace(1024, 0) == -1
     lib.sk_destroy(h)
     lib.sk_destroy(nul)
+    # flags: the ablation bit is accepted, unknown bits are not
+    assert lib.sk_init_ex(ctypes.byref(h), 100, 5, 1, 2) == _lib.SK_EINVAL
+    assert lib.sk_init_ex(ctypes.byref(h), 100, 5, 1, _lib.SK_FLAG_NO_PRECONDITION) == _lib.SK_OK
+    assert lib.sk_flags(h) == _lib.SK_FLAG_NO_PRECONDITION
+    assert lib.sk_kmeans2_assign(h, nul, 4, 100, nul, 3, nul, nul, nul) == _lib.SK_EINVAL
+    assert lib.sk_kmeans2_sums(h, nul, 4, 99, nul, 3, nul, nul, nul) == _lib.SK_EINVAL
+    assert b"ldx" in lib.sk_last_error()
+    assert lib.sk_mean_finalize(h, nul, 0, nul, nul) == _lib.SK_EINVAL
+    lib.sk_destroy(h)
+    assert lib.sk_flags(nul) == 0
