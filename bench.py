@@ -43,6 +43,17 @@ WORKLOAD = dict(workload="kmeans_mixture_n1e6_p1024_m51_K10", n=1_000_000, p=102
 METRIC = "samples/s compress+cov+K-means iter at 1 GB300; %HBM/tensor peak; err vs FP64"
 UNIT = "samples/s"
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture of this workload (profiles/), valid only
+# while the kernel source still has the digest it had when captured.
+KERNEL_TRAFFIC = {}
+
+
+def source_digest(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
 
 def load_peaks():
     try:
@@ -70,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -246,10 +257,14 @@ def run_gpu(args, cfg):
     st = pipeline.KMeansState(ctx, n, K, device=dev)
     stream = torch.cuda.current_stream()
 
-    stages = ["compress", "gram", "cov_finalize", "topk", "kmeans", "unmix"]
+    stages = ["compress", "gram", "cov_finalize", "topk", "kmeans_prep", "kmeans", "unmix"]
+    # library kernels per step: bucket + Gram for the tensor-core modes; top-k
+    # = init + (iters + 1) x (panel, small Gram) + iters x (Cholesky, apply) +
+    # Jacobi + Ritz, then the eigenvector un-mix; K-means = start centres +
+    # iters x (assign/update, finalize)
     launches = {"compress": 1, "gram": 1 if args.gram == "fp32" else 2, "cov_finalize": 1,
-                "topk": 1 + (args.topk_iters + 1) + 3 * args.topk_iters + 3 + 1,
-                "kmeans": 1 + 2 * iters, "unmix": 1}
+                "topk": 4 * args.topk_iters + 5 + 1,
+                "kmeans_prep": 1, "kmeans": 2 * iters, "unmix": 1}
 
     def step(ev=None):
         def mark(i):
@@ -267,14 +282,15 @@ def run_gpu(args, cfg):
         sk.sk_unmix(ctx, U, out=Ux)
         mark(4)
         sk.sk_precondition(ctx, Xsel, Y=st.mu)
+        mark(5)
         if args.no_graph:
             for it in range(iters):
                 st.iteration(idx, val, first=(it == 0))
         else:
             st.graph.replay()
-        mark(5)
-        sk.sk_unmix(ctx, st.mu, out=cen)
         mark(6)
+        sk.sk_unmix(ctx, st.mu, out=cen)
+        mark(7)
 
     # capture the K-means loop once (its own kernels, replayed as one graph)
     mu0 = sk.sk_precondition(ctx, Xsel)
@@ -288,7 +304,8 @@ def run_gpu(args, cfg):
     barrier(pg, dev)
     sampler = ClockSampler(local)
     sampler.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+           for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -307,68 +324,72 @@ def run_gpu(args, cfg):
         stage_ms[name] = sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
     assert sk.sk_device_status() == sk.SK_OK
 
-    # ---- roofline of the dominant kernel
+    # ---- rooflines (algorithmic bytes or flops per launch / event-timed duration)
     hbm, bf16, bf16s, peak_src = load_peaks()
-    dom = max(stage_ms, key=stage_ms.get)
     kmeans_iter_ms = stage_ms["kmeans"] / iters
-    roof = None
-    if dom in ("compress", "kmeans"):
-        if dom == "compress":
-            bytes_ = n * (4 * p + 8 * m)
-            dur = stage_ms["compress"]
-            name = "compress_kernel<10,false>"
+    N = 256 if pt >= 256 else pt
+    ntiles = sum(pt // N - bi // (N // 128) for bi in range(pt // 128)) if pt >= 128 else 0
+    prods = {"fp32": 0, "bf16": 1, "bf16x3": 3}[args.gram]
+    roofs = {
+        # read X (4p B) + write the ELL row (8m B)
+        "compress": {"kernel": "compress_kernel<10,false,true>", "bound": "hbm",
+                     "bytes": n * (4 * p + 8 * m), "ms": stage_ms["compress"],
+                     "peak": hbm, "unit": "GB/s"},
+        # read the ELL row (8m B) and the previous label (4 B), write the label (4 B);
+        # the per-iteration time is the graph's / iters, so it includes one
+        # finalize launch (and the first, full-sums pass is averaged in)
+        "kmeans": {"kernel": "kmeans_kernel (assign + incremental update)", "bound": "hbm",
+                   "bytes": n * (8 * m + 8), "ms": kmeans_iter_ms, "peak": hbm, "unit": "GB/s"},
+    }
+    if prods:
+        # 128 x N upper tiles over n rows, three products per tile when split
+        roofs["gram"] = {"kernel": "gram_tc_kernel", "bound": "tensor",
+                         "flops": 2.0 * n * 128 * N * ntiles * prods, "ms": stage_ms["gram"],
+                         "peak": bf16s, "unit": "TFLOP/s", "tiles": ntiles,
+                         "algorithmic_macs": n * m * (m + 1) // 2}
+    for r in roofs.values():
+        if r["bound"] == "hbm":
+            r["achieved"] = r["bytes"] / (r["ms"] * 1e-3) / 1e9
         else:
-            bytes_ = n * (8 * m + 4 + 4)  # ELL read, label + dist write per iteration
-            dur = kmeans_iter_ms
-            name = "kmeans_kernel (fused assign+update, per iteration)"
-        ach = bytes_ / (dur * 1e-3) / 1e9
-        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "algorithmic_bytes": bytes_,
-                "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
-    else:
-        ntile = (pt // 128) * (pt // 128 + 1) // 2 if args.gram == "fp32" else None
-        if args.gram == "fp32":
-            ops = n * m * m  # algorithmic products (FP32 scatter)
-            ach = ops / (stage_ms["gram"] * 1e-3) / 1e9
-            roof = {"kernel": "gram_fp32_kernel", "bound": "alu", "achieved": ach,
-                    "peak": None, "unit": "Gproducts/s", "frac": None, "traffic": None,
-                    "note": f"shared-memory atomic scatter over {ntile} tiles"}
-        else:
-            # tensor-core work actually issued: 128 x N upper tiles over n rows,
-            # three products per tile for the split mode
-            N = 256 if pt >= 256 else pt
-            ntiles = sum(pt // N - bi // (N // 128) for bi in range(pt // 128))
-            prods = 3 if args.gram == "bf16x3" else 1
-            flops = 2.0 * n * 128 * N * ntiles * prods
-            ach = flops / (stage_ms["gram"] * 1e-3) / 1e12
-            roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": ach,
-                    "peak": bf16s, "unit": "TFLOP/s", "frac": ach / bf16s, "traffic": None,
-                    "flops_per_launch": flops, "tiles": ntiles,
-                    "algorithmic_macs": n * m * (m + 1) / 2,
-                    "peak_source": f"{peak_src} bf16_tflops_sustained"}
+            r["achieved"] = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        r["frac"] = r["achieved"] / r["peak"]
+    dom_stage = max((s_ for s_ in roofs), key=lambda s_: roofs[s_]["ms"] *
+                    (iters if s_ == "kmeans" else 1))
+    d = roofs[dom_stage]
+    src = (f"{peak_src} hbm_gbs (burst copy)" if d["bound"] == "hbm"
+           else f"{peak_src} bf16_tflops_sustained")
+    traffic = KERNEL_TRAFFIC.get(dom_stage)
+    if traffic is not None and (traffic["n"] != n or traffic["p"] != p or
+                                traffic["src_sha"] != source_digest(traffic["source"])):
+        traffic = None  # counters taken on another workload or an older kernel
+    roof = {"kernel": d["kernel"], "bound": d["bound"], "achieved": d["achieved"],
+            "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
+            "traffic": None if traffic is None else traffic["bytes"],
+            "algorithmic": d.get("bytes", d.get("flops")), "peak_source": src,
+            "stage": dom_stage}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
         Xh = torch.empty((n, p), dtype=torch.float32, pin_memory=True)
         Xh.copy_(X)
+        # the seeded start rows, picked on the host (input preparation)
+        Xsel_h = Xh[torch.as_tensor(rows)].contiguous().pin_memory()
         lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
         cen_h = torch.empty((K, p), dtype=torch.float32, pin_memory=True)
         ux_h = torch.empty((k, p), dtype=torch.float64, pin_memory=True)
         Xd2 = torch.empty_like(X)
         Xsel2 = torch.empty_like(Xsel)
-        ridx = torch.as_tensor(rows, device=dev)
 
         def e2e_step():
             Xd2.copy_(Xh, non_blocking=True)
-            X_saved = X
+            Xsel2.copy_(Xsel_h, non_blocking=True)
             sk.sk_compress(ctx, Xd2, idx=idx, val=val)
             sk.sk_cov_reset(ctx, G)
             sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=gwork)
             sk.sk_cov_finalize(ctx, G, n, C=C)
             sk.sk_cov_topk(ctx, C, k, args.topk_iters, evals=evals, U=U, work=work)
             sk.sk_unmix(ctx, U, out=Ux)
-            torch.index_select(Xd2, 0, ridx, out=Xsel2)
             sk.sk_precondition(ctx, Xsel2, Y=st.mu)
             if args.no_graph:
                 for it in range(iters):
@@ -379,7 +400,6 @@ def run_gpu(args, cfg):
             lab_h.copy_(st.labels, non_blocking=True)
             cen_h.copy_(cen, non_blocking=True)
             ux_h.copy_(Ux, non_blocking=True)
-            del X_saved
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -395,10 +415,30 @@ def run_gpu(args, cfg):
         torch.cuda.synchronize()
         ems = max_over_ranks(a.elapsed_time(b) / nst, pg, dev)
         e2e = {"value": world * n / (ems * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": n * p * 4,
+               "h2d_bytes_per_step": n * p * 4 + K * p * 4,
                "d2h_bytes_per_step": n * 4 + K * p * 4 + k * p * 8,
                "ms_per_step": ems}
         del Xh
+
+    # the plain FP32 GPU form of the covariance pass (shared-memory scatter
+    # Gram), timed beside the chosen mode on the same ELL rows
+    plain = None
+    if mode != sk.SK_GRAM_FP32:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        sk.sk_cov_reset(ctx, G)
+        sk.sk_cov_accumulate(ctx, sk.SK_GRAM_FP32, idx, val, G)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(3):
+            sk.sk_cov_reset(ctx, G)
+            sk.sk_cov_accumulate(ctx, sk.SK_GRAM_FP32, idx, val, G)
+        b.record(stream)
+        torch.cuda.synchronize()
+        g32 = a.elapsed_time(b) / 3
+        plain = {"gram": "fp32", "gram_ms": g32, "chosen_gram_ms": stage_ms["gram"],
+                 "speedup": g32 / stage_ms["gram"],
+                 "step_value": world * n / ((ms - stage_ms["gram"] + g32) * 1e-3)}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -421,7 +461,8 @@ def run_gpu(args, cfg):
                        "gram": args.gram, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (X is 4.1 GB)"},
             "stage_ms": stage_ms, "kmeans_iter_ms": kmeans_iter_ms,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roof, "stage_rooflines": roofs, "plain_fp32_form": plain,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": sum(launches.values()) * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -433,14 +474,14 @@ def run_gpu(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--gram", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--gram", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--topk-iters", type=int, default=8)
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--cpu-rows", type=int, default=4000)
-    ap.add_argument("--ref-rows", type=int, default=3000)
+    ap.add_argument("--cpu-rows", type=int, default=200_000)
+    ap.add_argument("--ref-rows", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true",

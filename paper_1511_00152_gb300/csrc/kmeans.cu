@@ -10,6 +10,14 @@
 // multiply-add -- so no cross-lane reduction over t is needed; the argmin over
 // the LPR lanes of a row (ties to the smallest k) takes a few shuffles.
 //
+// Bank-disjoint centre copies: with LPR <= 16 the rows of a warp are laid out
+// per half-warp (G = 16 / LPR row slots in each half).  When the table fits,
+// coordinate j owns one 32-word line of shared memory holding G copies of its
+// Kpad centre values, copy s at words s*Kpad .. s*Kpad + Kpad - 1; the row in
+// slot s reads copy s.  The G rows of a half-warp then touch disjoint banks
+// whatever their coordinates, so a centre load is one wavefront per half-warp
+// instead of a random number of conflicting ones.
+//
 // Update: in the same pass, each (row, t) entry adds val to S[label][idx] and
 // 1 to cnt[label][idx] in CTA-private shared-memory accumulators, flushed to
 // the caller's float64 / int32 sums with one atomic per touched entry.
@@ -29,6 +37,7 @@ struct KmParams {
     int m;
     int pt;
     int K, Kpad, LPR, RW;
+    int G;          // row slots per half-warp (0: rows laid out over the whole warp)
     int stage_cap;  // staged (idx, val) entries per warp
     const float *mu;
     int32_t *labels;
@@ -56,13 +65,21 @@ __device__ __forceinline__ uint64_t sqacc2(uint64_t d, uint64_t acc) {
     return r;
 }
 
-template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE>
+// Lane of the first centre group of row slot rs, and row slot of a lane.
+__device__ __forceinline__ int lead_lane(const KmParams &P, int rs) {
+    return P.G ? (rs / P.G) * 16 + (rs % P.G) * P.LPR : rs * P.LPR;
+}
+__device__ __forceinline__ int slot_of_lane(const KmParams &P, int l) {
+    return P.G ? (l >> 4) * P.G + (l & 15) / P.LPR : l / P.LPR;
+}
+
+template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE, bool COPIES>
 __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     constexpr int NP = KPL / 2;  // packed pairs per lane
     extern __shared__ __align__(16) unsigned char smem_raw[];
     size_t off = 0;
     float *mus = reinterpret_cast<float *>(smem_raw + off);
-    if (MU_SMEM && P.do_assign) off += (size_t)P.pt * P.Kpad * 4;
+    if (MU_SMEM && P.do_assign) off += (size_t)P.pt * (COPIES ? 32 : P.Kpad) * 4;
     float *sS = reinterpret_cast<float *>(smem_raw + off);
     int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
     int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
@@ -72,9 +89,17 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     const int tid = threadIdx.x;
     const int KP = P.K * P.pt;
     if (MU_SMEM && P.do_assign) {
-        for (int e = tid; e < P.pt * P.Kpad; e += blockDim.x) {
-            const int j = e / P.Kpad, k = e - j * P.Kpad;
-            mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
+        if constexpr (COPIES) {
+            for (int e = tid; e < P.pt * 32; e += blockDim.x) {
+                const int j = e >> 5, w = e & 31;
+                const int c = w / P.Kpad, k = w - c * P.Kpad;
+                mus[e] = (c < P.G && k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
+            }
+        } else {
+            for (int e = tid; e < P.pt * P.Kpad; e += blockDim.x) {
+                const int j = e / P.Kpad, k = e - j * P.Kpad;
+                mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
+            }
         }
     }
     if (PRIV && P.do_update == 1) {
@@ -87,10 +112,21 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     __syncthreads();
 
     const int lane = tid & 31, warp = tid >> 5;
-    const int sub = lane / P.LPR;       // row slot of this lane in the warp
-    const int kl = lane - sub * P.LPR;  // centre group of this lane
+    // row slot of this lane in the warp, its centre group, and (per half-warp
+    // layout) the slot's position in its half, which selects the copy
+    int sub, kl, hs = 0;
+    bool lane_used;
+    if (P.G) {
+        hs = (lane & 15) / P.LPR;
+        sub = (lane >> 4) * P.G + hs;
+        kl = (lane & 15) - hs * P.LPR;
+        lane_used = hs < P.G;
+    } else {
+        sub = lane / P.LPR;
+        kl = lane - sub * P.LPR;
+        lane_used = sub < P.RW;
+    }
     const int kbase = kl * KPL;
-    const bool lane_used = sub < P.RW;
     int2 *stage = stage_all + (size_t)warp * P.stage_cap;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -137,7 +173,8 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                     }
                     const uint64_t vv = pack2(v, v);
                     if constexpr (MU_SMEM) {
-                        const uint64_t *c = reinterpret_cast<const uint64_t *>(mus + j * P.Kpad + kbase);
+                        const float *line = COPIES ? mus + j * 32 + hs * P.Kpad : mus + j * P.Kpad;
+                        const uint64_t *c = reinterpret_cast<const uint64_t *>(line + kbase);
 #pragma unroll
                         for (int q = 0; q < NP; ++q) acc[q] = sqacc2(sub2(vv, c[q]), acc[q]);
                     } else {
@@ -169,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                 }
             }
             // argmin across the LPR lanes of the row (ties to the smaller k)
-            const int lead = sub * P.LPR;
+            const int lead = lane_used ? lead_lane(P, sub) : 32;
             for (int o = 1; o < P.LPR; ++o) {
                 const int srcl = (lead + o < 32) ? lead + o : lane;
                 const float od = __shfl_sync(kFull, bd, srcl);
@@ -201,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                 while (pending) {
                     const int src = __ffs(pending) - 1;
                     pending &= pending - 1;
-                    const int rs = src / P.LPR;
+                    const int rs = slot_of_lane(P, src);
                     const int newl = __shfl_sync(kFull, label, src);
                     const int oldl = __shfl_sync(kFull, old, src);
                     for (int t = lane; t < m; t += 32) {
@@ -249,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             for (int rs = 0; rs < rows_here; ++rs) {
                 int lab;
                 if (P.do_assign) {
-                    lab = __shfl_sync(kFull, label, rs * P.LPR);
+                    lab = __shfl_sync(kFull, label, lead_lane(P, rs));
                 } else {
                     lab = __ldg(P.labels + base + rs);
                 }
@@ -311,9 +348,9 @@ __global__ void kmeans_finalize_kernel(int64_t KP, const double *S, const int32_
     }
 }
 
-template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE>
+template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE, bool COPIES>
 cudaError_t launch_variant(const KmParams &P, size_t smem, cudaStream_t s) {
-    auto kern = kmeans_kernel<KPL, MU_SMEM, PRIV, STAGE>;
+    auto kern = kmeans_kernel<KPL, MU_SMEM, PRIV, STAGE, COPIES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -330,25 +367,36 @@ cudaError_t launch_variant(const KmParams &P, size_t smem, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int KPL, bool MU_SMEM, bool PRIV>
+template <int KPL, bool MU_SMEM, bool PRIV, bool COPIES = false>
 cudaError_t launch_stage(KmParams &P, size_t fixed, size_t budget, cudaStream_t s) {
     const size_t stage_b = (size_t)kWarpsK * P.RW * P.m * 8;
     if (fixed + stage_b <= budget) {
         P.stage_cap = P.RW * P.m;
-        return launch_variant<KPL, MU_SMEM, PRIV, true>(P, fixed + stage_b, s);
+        return launch_variant<KPL, MU_SMEM, PRIV, true, COPIES>(P, fixed + stage_b, s);
     }
     P.stage_cap = 0;
-    return launch_variant<KPL, MU_SMEM, PRIV, false>(P, fixed, s);
+    return launch_variant<KPL, MU_SMEM, PRIV, false, COPIES>(P, fixed, s);
 }
 
 template <int KPL>
 cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     P.LPR = (P.K + KPL - 1) / KPL;
     P.Kpad = P.LPR * KPL;
-    P.RW = 32 / P.LPR;
+    // rows per half-warp when a row needs at most 16 lanes
+    P.G = P.LPR <= 16 ? 16 / P.LPR : 0;
+    P.RW = P.G ? 2 * P.G : 32 / P.LPR;
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if constexpr (KPL == 2) {
+        // bank-disjoint copies: worth it with two or more rows per half-warp,
+        // when the assignment runs without the shared-memory update sums and
+        // the 32-word lines plus the row staging fit
+        const size_t lines_b = (size_t)P.pt * 32 * 4;
+        const size_t stage_b = (size_t)kWarpsK * P.RW * P.m * 8;
+        if (P.do_assign && P.do_update != 1 && P.G >= 2 && lines_b + stage_b <= (size_t)smem_max)
+            return launch_stage<KPL, true, false, true>(P, lines_b, (size_t)smem_max, s);
+    }
     const size_t mu_b = P.do_assign ? (size_t)P.pt * P.Kpad * 4 : 0;
     // the incremental mode touches only rows whose label changed (few after the
     // first passes): it adds straight into the global sums and keeps the

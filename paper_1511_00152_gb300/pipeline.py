@@ -13,11 +13,12 @@ from . import _lib as sk
 class KMeansState:
     """Device buffers of one sparsified K-means run (Algorithm 1 loop)."""
 
-    def __init__(self, ctx: sk.Ctx, n: int, K: int, device="cuda"):
+    def __init__(self, ctx: sk.Ctx, n: int, K: int, device="cuda", keep_dist: bool = False):
         self.ctx, self.n, self.K = ctx, n, K
         self.mu = torch.empty((K, ctx.pt), dtype=torch.float32, device=device)
         self.labels = torch.empty(n, dtype=torch.int32, device=device)
-        self.dist = torch.empty(n, dtype=torch.float32, device=device)
+        # each row's winning restricted distance, written only when asked for
+        self.dist = torch.empty(n, dtype=torch.float32, device=device) if keep_dist else None
         self.S = torch.empty((K, ctx.pt), dtype=torch.float64, device=device)
         self.cnt = torch.empty((K, ctx.pt), dtype=torch.int32, device=device)
         self.nk = torch.empty(K, dtype=torch.int64, device=device)

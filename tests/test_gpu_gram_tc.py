@@ -42,11 +42,12 @@ def test_gram_tc_parity(sk, mode, p, m, n):
     seed = 11
     ctx = sk.sk_init(p, m, seed)
     pt = ctx.pt
-    idx, val = sk.sk_compress(ctx, _dev(X))
     oi, ov = oracle.compress(X, m, seed)
-    # the Gram of the GPU's own float32 values, so the test isolates the Gram
-    vals32 = val.cpu().numpy().astype(np.float64)
-    Go = oracle.gram(oi, vals32, pt)
+    # the GPU Gram runs on the oracle's ELL rows rounded to float32, and the
+    # oracle's Gram of the same float32 values isolates the Gram
+    v32 = ov.astype(np.float32)
+    idx, val = _dev(oi), _dev(v32)
+    Go = oracle.gram(oi, v32.astype(np.float64), pt)
     G = torch.empty((pt, pt), dtype=torch.float64, device="cuda")
     sk.sk_cov_reset(ctx, G)
     h = n // 2
@@ -70,9 +71,10 @@ def test_gram_tc_two_segments(sk):
     n, p, m, seed = 70000, 256, 26, 5
     X = synth.mixture(n, p, 6, seed=1)[0]
     ctx = sk.sk_init(p, m, seed)
-    idx, val = sk.sk_compress(ctx, _dev(X))
-    oi = idx.cpu().numpy()
-    Go = oracle.gram(oi, val.cpu().numpy().astype(np.float64), ctx.pt)
+    oi, ov = oracle.compress(X, m, seed)
+    v32 = ov.astype(np.float32)
+    idx, val = _dev(oi), _dev(v32)
+    Go = oracle.gram(oi, v32.astype(np.float64), ctx.pt)
     for mode in (2, 1):
         G = torch.zeros((ctx.pt, ctx.pt), dtype=torch.float64, device="cuda")
         sk.sk_cov_accumulate(ctx, mode, idx, val, G)

@@ -196,12 +196,15 @@ def test_kmeans_end_to_end_tiny(sk):
     # graph replay reproduces the eager loop
     st2 = pipeline.KMeansState(ctx, n, K)
     l2, mu2 = st2.run(idx, val, mu0, iters=10, use_graph=False)
-    assert torch.equal(l2, labels)
-    assert torch.allclose(mu2, mu, rtol=1e-6, atol=1e-7)
-    # un-mixed centres
-    um = sk.sk_unmix(ctx, mu).cpu().numpy().astype(np.float64)
-    umo = oracle.unmix(mu.cpu().numpy().astype(np.float64), p, seed)
-    assert np.abs(um - umo).max() <= 1e-5 * np.abs(umo).max()
+    # the float atomics of the centre sums add in a run-dependent order, so
+    # the two runs agree up to that rounding (and any near-tie it flips)
+    assert float((l2 == labels).float().mean()) >= 0.999
+    assert torch.allclose(mu2, mu, rtol=1e-5, atol=1e-6)
+    # un-mixed centres, end to end against the oracle's own run
+    if agree == 1.0:
+        um = sk.sk_unmix(ctx, mu).cpu().numpy().astype(np.float64)
+        umo = oracle.unmix(muo, p, seed)
+        assert np.abs(um - umo).max() <= 1e-5 * np.abs(umo).max()
 
 
 @pytest.mark.parametrize("p,m,n", [(64, 8, 2000), (1024, 51, 3000), (300, 20, 1000), (4096, 205, 200),
@@ -335,7 +338,11 @@ def test_kmeans_incremental_sums_match_recomputed(sk, p, m, n, K):
     seed = 29
     ctx = sk.sk_init(p, m, seed)
     Xd = _dev(X)
-    idx, val = sk.sk_compress(ctx, Xd)
+    # the ELL rows are the oracle's (rounded to float32), so the expected sums
+    # below are computed from inputs, never from a GPU result
+    oi, ov = oracle.compress(X, m, seed)
+    v32 = ov.astype(np.float32)
+    idx, val = _dev(oi), _dev(v32)
     rows = synth.init_rows(n, K, seed)
     mu0 = pipeline.initial_centres(ctx, Xd, rows)
     a = pipeline.KMeansState(ctx, n, K)
@@ -348,15 +355,17 @@ def test_kmeans_incremental_sums_match_recomputed(sk, p, m, n, K):
     assert agree >= 0.999, agree
     if agree == 1.0:
         assert torch.allclose(mua, mub, rtol=1e-5, atol=1e-6)
-    # the running sums describe the final labels exactly
-    oi = idx.cpu().numpy()
-    ov = val.cpu().numpy().astype(np.float64)
-    labs = a.labels.cpu().numpy()
-    mu_prev = np.zeros((K, ctx.pt))
-    _mu, counts_o, nk_o = oracle.kmeans_update(oi, ov, labs, mu_prev, ctx.pt)
+    # the running sums describe the final labels exactly (Eq. (mu_update_one)
+    # written out with numpy over the input rows and the final labels)
+    labs = a.labels.cpu().numpy().astype(np.int64)
+    lk = np.repeat(labs, m)
+    counts_o = np.zeros((K, ctx.pt), np.int64)
+    So = np.zeros((K, ctx.pt))
+    np.add.at(counts_o, (lk, oi.ravel()), 1)
+    np.add.at(So, (lk, oi.ravel()), v32.astype(np.float64).ravel())
+    nk_o = np.bincount(labs, minlength=K)
     assert np.array_equal(a.cnt.cpu().numpy(), counts_o)
     assert np.array_equal(a.nk.cpu().numpy(), nk_o)
     # the first pass sums per-CTA float partials, later passes add FP64 deltas
-    So = np.where(counts_o > 0, _mu * counts_o, 0.0)
     assert np.abs(a.S.cpu().numpy() - So).max() <= 1e-5 * (np.abs(So).max() + 1e-30)
     assert int(a.changed.item()) > 0
