@@ -53,6 +53,40 @@ __device__ __forceinline__ uint32_t sign_bit(uint32_t k0, uint32_t k1, uint32_t 
     return (pick_word(o, (j >> 5) & 3u) >> (j & 31u)) & 1u;
 }
 
+// float64 reciprocal square root and reciprocal by Newton-Raphson.
+// The argument is split as m 2^(2k) (m in [1, 4)) or m 2^e (m in [1, 2)) so
+// the float32 estimate of the mantissa part is always in range; two
+// Newton-Raphson steps (y <- y (3 - m y^2) / 2, resp. y <- y (2 - m y)) take
+// its ~22 correct bits past float64 precision; the exponent is then restored.
+// For positive (resp. nonzero) normal x with |exponent| <= 1022; accurate to
+// a few units in the last place, not correctly rounded.
+__device__ __forceinline__ double pow2(int e) {  // 2^e for -1022 <= e <= 1023
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    const int k = e >> 1;  // floor(e / 2)
+    const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) |
+                                          ((long long)(e - 2 * k + 1023) << 52));
+    double y = (double)rsqrtf((float)m);
+    const double hm = 0.5 * m;
+    y = y * (1.5 - hm * y * y);
+    y = y * (1.5 - hm * y * y);
+    return y * pow2(-k);
+}
+
+__device__ __forceinline__ double rcp_nr(double x) {
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    const double m = __longlong_as_double((bits & 0x800fffffffffffffLL) | (1023LL << 52));
+    double y = (double)__frcp_rn((float)m);
+    y = y * (2.0 - m * y);
+    y = y * (2.0 - m * y);
+    return y * pow2(-e);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
