@@ -4,7 +4,9 @@
 //
 // Block subspace iteration with b = min(pt, 64, max(k + 8, 2k)) columns:
 //   W = C V;  V = W R^{-1} with R the Cholesky factor of W^T W (CholQR),
-// repeated `iters` times from a seeded start, then one Rayleigh-Ritz step:
+// repeated `iters` times (at least once) from a seeded start, the last
+// CholQR in float64 and the earlier ones from a float32 factor (see
+// chol32_kernel), then one Rayleigh-Ritz step:
 // H = V^T C V (b x b), H = Q diag(lambda) Q^T, and U = V Q restricted to the
 // k largest lambda.  Each eigenvector's sign makes its largest-magnitude
 // entry positive.
@@ -203,6 +205,73 @@ __global__ void __launch_bounds__(kApplyThreads) apply_solve_kernel(const double
     }
 }
 
+// Intermediate CholQR in float32.  In the iterations before the last, V
+// only has to be a well-conditioned basis of span(W): V = W M for any
+// invertible M keeps the span exactly (the combination is formed in
+// float64).  So M = R^{-1} is taken from a float32 Cholesky of the
+// diagonally scaled Gram S = D Gm D (D = diag(Gm)^{-1/2}, unit diagonal, so
+// float32 range is never an issue), M = D R_S^{-1}; V is then orthonormal
+// to float32 accuracy, and the last iteration re-orthonormalises in float64.
+__global__ void __launch_bounds__(256) chol32_kernel(const double *Gm, int b, double *Minv) {
+    __shared__ float A[kMaxB][kMaxB + 1];
+    __shared__ float X[kMaxB][kMaxB + 1];
+    __shared__ double d[kMaxB];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int c = tid; c < b; c += nt) {
+        const double g = Gm[c * b + c];
+        d[c] = g > 1e-300 ? rsqrt_nr(g) : 1.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < b * b; e += nt) {
+        const int r = e / b, c = e % b;
+        A[r][c] = (float)(Gm[e] * d[r] * d[c]);
+    }
+    __syncthreads();
+    for (int c = 0; c < b; ++c) {
+        if (tid == 0) A[c][c] = sqrtf(fmaxf(A[c][c], 1e-12f));
+        __syncthreads();
+        const float inv = 1.0f / A[c][c];
+        for (int j = c + 1 + tid; j < b; j += nt) A[c][j] *= inv;
+        __syncthreads();
+        const int rem = b - c - 1;
+        for (int w = tid; w < rem * rem; w += nt) {
+            const int i = c + 1 + w / rem, j = c + 1 + w % rem;
+            if (j >= i) A[i][j] -= A[c][i] * A[c][j];
+        }
+        __syncthreads();
+    }
+    // X = R_S^{-1} (upper) by back substitution, a thread per column
+    for (int j = tid; j < b; j += nt) {
+        for (int i = j; i >= 0; --i) {
+            float s = (i == j) ? 1.0f : 0.0f;
+            for (int q = i + 1; q <= j; ++q) s -= A[i][q] * X[q][j];
+            X[i][j] = s / A[i][i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < b * b; e += nt) {
+        const int q = e / b, c = e % b;
+        Minv[e] = (c >= q) ? d[q] * (double)X[q][c] : 0.0;
+    }
+}
+
+// V[c*pt + i] = sum_{q <= c} W[q*pt + i] Minv[q*b + c], a thread per (c, i).
+__global__ void __launch_bounds__(256) apply_minv_kernel(const double *W, const double *Minv,
+                                                        int64_t pt, int b, double *V) {
+    __shared__ double Ms[kMaxB * kMaxB];
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Ms[e] = Minv[e];
+    __syncthreads();
+    const int64_t total = (int64_t)b * pt;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / pt);
+        const int64_t i = e - (int64_t)c * pt;
+        double s = 0.0;
+        for (int q = 0; q <= c; ++q) s = fma(W[(int64_t)q * pt + i], Ms[q * b + c], s);
+        V[e] = s;
+    }
+}
+
 // ---- cyclic Jacobi on a b x b symmetric matrix in shared memory, one CTA.
 // Parallel (round-robin) ordering: each step applies bp/2 disjoint plane
 // rotations at once (bp = b rounded up to even; the extra index is a
@@ -341,8 +410,8 @@ struct RitzSmem {
     JacobiScratch js;
 };
 
-__global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b, double *Qout,
-                                                      double *lam) {
+__global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b, int k,
+                                                      double *Qout, double *lam, double *ord) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RitzSmem &S = *reinterpret_cast<RitzSmem *>(smem_raw);
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -355,7 +424,9 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b,
         S.Q32[r][c] = (r == c) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    jacobi_dev<float, kMaxB + 1, kMaxB>(S.A32, S.Q32, b, 40, 1e-12, S.js);
+    // float32 Jacobi stalls near float32 rounding (off-diagonal mass around
+    // 1e-13 of the total), so it stops at 1e-10 or after 12 sweeps
+    jacobi_dev<float, kMaxB + 1, kMaxB>(S.A32, S.Q32, b, 12, 1e-10, S.js);
     // G = Q32^T Q32 in float64
     for (int e = tid; e < b * b; e += nt) {
         const int i = e / b, j = e % b;
@@ -395,7 +466,9 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b,
         if (r < b && c < b) S.Qb[r][c] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_dev<double, kMaxB + 1, kMaxB>(S.A64, S.Qb, b, 30, 1e-30, S.js);
+    // the polish starts from off-diagonal mass ~1e-10..1e-14 of the total;
+    // one or two sweeps reach 1e-26 (eigenvector directions to ~1e-13 / gap)
+    jacobi_dev<double, kMaxB + 1, kMaxB>(S.A64, S.Qb, b, 30, 1e-26, S.js);
     for (int e = tid; e < b * b; e += nt) {
         const int r = e / b, c = e % b;
         double s = 0.0;
@@ -403,40 +476,56 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b,
         Qout[e] = s;
     }
     for (int r = tid; r < b; r += nt) lam[r] = S.A64[r][r];
+    // indices of the k largest eigenvalues, descending (ties by lower index)
+    if (tid == 0) {
+        unsigned long long used = 0ull;
+        for (int c = 0; c < k; ++c) {
+            int pick = -1;
+            for (int q = 0; q < b; ++q)
+                if (!((used >> q) & 1ull) && (pick < 0 || S.A64[q][q] > S.A64[pick][pick])) pick = q;
+            used |= 1ull << pick;
+            ord[c] = (double)pick;
+        }
+    }
 }
 
-// U[c*pt + i] = sum_q V[q*pt + i] Q[q*b + order[c]] for the k largest lambda,
-// then the sign convention.  One CTA per output column c.
-__global__ void ritz_out_kernel(const double *V, const double *Q, const double *lam,
-                                int64_t pt, int b, int k, double *U, double *evals) {
-    __shared__ int order_c;
+// U[c*pt + i] = sum_q V[q*pt + i] Q[q*b + ord[c]] and evals[c] = lam[ord[c]],
+// a thread per (c, i).
+__global__ void __launch_bounds__(256) ritz_u_kernel(const double *V, const double *Q,
+                                                    const double *lam, const double *ord,
+                                                    int64_t pt, int b, int k, double *U,
+                                                    double *evals) {
+    __shared__ double Qs[kMaxB * kMaxB];
+    __shared__ int os[kMaxB];
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Qs[e] = Q[e];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) os[c] = (int)ord[c];
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < k; c += blockDim.x) evals[c] = lam[os[c]];
+    const int64_t total = (int64_t)k * pt;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / pt);
+        const int64_t i = e - (int64_t)c * pt;
+        const int col = os[c];
+        double s = 0.0;
+        for (int q = 0; q < b; ++q) s = fma(V[(int64_t)q * pt + i], Qs[q * b + col], s);
+        U[e] = s;
+    }
+}
+
+// Sign convention: each eigenvector's largest-magnitude entry (lowest index
+// on ties) is made positive.  One CTA per vector.
+__global__ void __launch_bounds__(256) sign_fix_kernel(int64_t pt, double *U) {
     __shared__ double red_v[256];
     __shared__ int64_t red_i[256];
-    const int c = blockIdx.x;
-    if (threadIdx.x == 0) {
-        // c-th largest eigenvalue (ties by lower index)
-        bool used[kMaxB];
-        for (int q = 0; q < b; ++q) used[q] = false;
-        int pick = 0;
-        for (int r = 0; r <= c; ++r) {
-            pick = -1;
-            for (int q = 0; q < b; ++q)
-                if (!used[q] && (pick < 0 || lam[q] > lam[pick])) pick = q;
-            used[pick] = true;
-        }
-        order_c = pick;
-        evals[c] = lam[pick];
-    }
-    __syncthreads();
-    const int col = order_c;
+    double *u = U + (int64_t)blockIdx.x * pt;
     double best = -1.0;
     int64_t besti = 0;
     for (int64_t i = threadIdx.x; i < pt; i += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < b; ++q) s = fma(V[(int64_t)q * pt + i], Q[q * b + col], s);
-        U[(int64_t)c * pt + i] = s;
-        if (fabs(s) > best) {
-            best = fabs(s);
+        const double a = fabs(u[i]);
+        if (a > best) {
+            best = a;
             besti = i;
         }
     }
@@ -454,10 +543,10 @@ __global__ void ritz_out_kernel(const double *V, const double *Q, const double *
         }
         __syncthreads();
     }
-    const bool flip = U[(int64_t)c * pt + red_i[0]] < 0.0;
+    const bool flip = u[red_i[0]] < 0.0;
     __syncthreads();
     if (flip)
-        for (int64_t i = threadIdx.x; i < pt; i += blockDim.x) U[(int64_t)c * pt + i] *= -1.0;
+        for (int64_t i = threadIdx.x; i < pt; i += blockDim.x) u[i] = -u[i];
 }
 
 }  // namespace
@@ -550,22 +639,34 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     e = cudaFuncSetAttribute(ritz_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(RitzSmem));
     if (e != cudaSuccess) return e;
+    int mblocks = (int)((b * pt + 255) / 256);
+    if (mblocks > 4 * sms) mblocks = 4 * sms;
+    int ublocks = (int)((k * pt + 255) / 256);
+    if (ublocks > 4 * sms) ublocks = 4 * sms;
+    // at least one CholQR, the last one in float64
+    const int n_it = iters > 0 ? iters : 1;
     init_v_kernel<<<eblocks, 256, 0, s>>>(w.V, pt, b, k0, k1);
-    for (int it = 0; it <= iters; ++it) {
+    for (int it = 0; it <= n_it; ++it) {
         e = cudaMemsetAsync(w.W, 0, (size_t)b * pt * sizeof(double), s);
         if (e != cudaSuccess) return e;
         e = panel(pgrid, C, w.V, pt, b, jlen, w.W, s);
         if (e != cudaSuccess) return e;
-        if (it == iters) break;
+        if (it == n_it) break;
         small_gram_kernel<<<b * b, 256, 0, s>>>(w.W, w.W, pt, b, w.Gm);
-        chol_kernel<<<1, 256, 0, s>>>(w.Gm, b, w.R, w.lam);
-        apply_solve_kernel<<<ablocks, kApplyThreads, apply_smem, s>>>(w.W, w.R, w.lam, pt, b,
-                                                                      w.V);
+        if (it < n_it - 1) {
+            chol32_kernel<<<1, 256, 0, s>>>(w.Gm, b, w.R);
+            apply_minv_kernel<<<mblocks, 256, 0, s>>>(w.W, w.R, pt, b, w.V);
+        } else {
+            chol_kernel<<<1, 256, 0, s>>>(w.Gm, b, w.R, w.lam);
+            apply_solve_kernel<<<ablocks, kApplyThreads, apply_smem, s>>>(w.W, w.R, w.lam, pt,
+                                                                          b, w.V);
+        }
     }
-    // Rayleigh-Ritz: H = V^T (C V)
+    // Rayleigh-Ritz: H = V^T (C V); the order of the k largest goes to Gm
     small_gram_kernel<<<b * b, 256, 0, s>>>(w.V, w.W, pt, b, w.H);
-    ritz_eig_kernel<<<1, 256, sizeof(RitzSmem), s>>>(w.H, b, w.Q, w.lam);
-    ritz_out_kernel<<<k, 256, 0, s>>>(w.V, w.Q, w.lam, pt, b, k, U, evals);
+    ritz_eig_kernel<<<1, 256, sizeof(RitzSmem), s>>>(w.H, b, k, w.Q, w.lam, w.Gm);
+    ritz_u_kernel<<<ublocks, 256, 0, s>>>(w.V, w.Q, w.lam, w.Gm, pt, b, k, U, evals);
+    sign_fix_kernel<<<k, 256, 0, s>>>(pt, U);
     return cudaGetLastError();
 }
 
