@@ -39,7 +39,6 @@ struct KmParams {
     int K, Kpad, LPR, RW;
     int G;          // row slots per half-warp (0: rows laid out over the whole warp)
     int stage_cap;  // staged (idx, val) entries per warp
-    int sstride;    // staged entries per row (>= m)
     const float *mu;
     int32_t *labels;
     float *dist;
@@ -138,18 +137,11 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
         const int rows_here = (int)((P.n - base) < P.RW ? (P.n - base) : P.RW);
         if constexpr (STAGE) {
             // this pass's rows are contiguous in the ELL arrays: coalesced copy
+            const int total = rows_here * m;
             const int32_t *gi = P.idx + base * m;
             const float *gv = P.val + base * m;
-            if (P.sstride == m) {
-                const int total = rows_here * m;
-                for (int e = lane; e < total; e += 32)
-                    stage[e] = make_int2(__ldg(gi + e), __float_as_int(__ldg(gv + e)));
-            } else {
-                for (int r = 0; r < rows_here; ++r)
-                    for (int t = lane; t < m; t += 32)
-                        stage[r * P.sstride + t] = make_int2(__ldg(gi + r * m + t),
-                                                             __float_as_int(__ldg(gv + r * m + t)));
-            }
+            for (int e = lane; e < total; e += 32)
+                stage[e] = make_int2(__ldg(gi + e), __float_as_int(__ldg(gv + e)));
             __syncwarp();
         }
         const int64_t i = base + sub;
@@ -163,33 +155,8 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
             uint64_t acc[NP];
 #pragma unroll
             for (int q = 0; q < NP; ++q) acc[q] = 0ull;
-            if (COPIES && STAGE && MU_SMEM && row_ok) {
-                // two steps per 16-byte staged load (row stride even, rows on
-                // distinct bank quads)
-                const int2 *rs = stage + sub * P.sstride;
-                const float *tab = mus + hs * P.Kpad + kbase;
-                int t = 0;
-#pragma unroll 2
-                for (; t + 1 < m; t += 2) {
-                    const int4 iv2 = *reinterpret_cast<const int4 *>(rs + t);
-                    const uint64_t *c0 = reinterpret_cast<const uint64_t *>(tab + (iv2.x & pmask) * 32);
-                    const uint64_t *c1 = reinterpret_cast<const uint64_t *>(tab + (iv2.z & pmask) * 32);
-                    const float v0 = __int_as_float(iv2.y), v1 = __int_as_float(iv2.w);
-                    const uint64_t vv0 = pack2(v0, v0), vv1 = pack2(v1, v1);
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) acc[q] = sqacc2(sub2(vv0, c0[q]), acc[q]);
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) acc[q] = sqacc2(sub2(vv1, c1[q]), acc[q]);
-                }
-                if (t < m) {
-                    const int2 iv = rs[t];
-                    const uint64_t *c = reinterpret_cast<const uint64_t *>(tab + (iv.x & pmask) * 32);
-                    const uint64_t vv = pack2(__int_as_float(iv.y), __int_as_float(iv.y));
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) acc[q] = sqacc2(sub2(vv, c[q]), acc[q]);
-                }
-            } else if (row_ok) {
-                const int2 *rs = stage + sub * P.sstride;
+            if (row_ok) {
+                const int2 *rs = stage + sub * m;
                 const int32_t *ri = P.idx + i * m;
                 const float *rv = P.val + i * m;
 #pragma unroll 4
@@ -278,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                         int j;
                         float v;
                         if constexpr (STAGE) {
-                            const int2 iv = stage[rs * P.sstride + t];
+                            const int2 iv = stage[rs * m + t];
                             j = iv.x & pmask;
                             v = __int_as_float(iv.y);
                         } else {
@@ -329,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
                     int j;
                     float v;
                     if constexpr (STAGE) {
-                        const int2 iv = stage[rs * P.sstride + t];
+                        const int2 iv = stage[rs * m + t];
                         j = iv.x & pmask;
                         v = __int_as_float(iv.y);
                     } else {
@@ -402,9 +369,9 @@ cudaError_t launch_variant(const KmParams &P, size_t smem, cudaStream_t s) {
 
 template <int KPL, bool MU_SMEM, bool PRIV, bool COPIES = false>
 cudaError_t launch_stage(KmParams &P, size_t fixed, size_t budget, cudaStream_t s) {
-    const size_t stage_b = (size_t)kWarpsK * P.RW * P.sstride * 8;
+    const size_t stage_b = (size_t)kWarpsK * P.RW * P.m * 8;
     if (fixed + stage_b <= budget) {
-        P.stage_cap = P.RW * P.sstride;
+        P.stage_cap = P.RW * P.m;
         return launch_variant<KPL, MU_SMEM, PRIV, true, COPIES>(P, fixed + stage_b, s);
     }
     P.stage_cap = 0;
@@ -421,21 +388,14 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    P.sstride = P.m;
     if constexpr (KPL == 2) {
         // bank-disjoint copies: worth it with two or more rows per half-warp,
         // when the assignment runs without the shared-memory update sums and
-        // the 32-word lines plus the row staging fit.  Staged rows get an even
-        // stride that is not a multiple of 16 (int2 units): 16-byte loads of
-        // two entries, consecutive rows on distinct bank quads.
-        int sstride = (P.m + 1) & ~1;
-        if (sstride % 16 == 0) sstride += 2;
+        // the 32-word lines plus the row staging fit
         const size_t lines_b = (size_t)P.pt * 32 * 4;
-        const size_t stage_b = (size_t)kWarpsK * P.RW * sstride * 8;
-        if (P.do_assign && P.do_update != 1 && P.G >= 2 && lines_b + stage_b <= (size_t)smem_max) {
-            P.sstride = sstride;
+        const size_t stage_b = (size_t)kWarpsK * P.RW * P.m * 8;
+        if (P.do_assign && P.do_update != 1 && P.G >= 2 && lines_b + stage_b <= (size_t)smem_max)
             return launch_stage<KPL, true, false, true>(P, lines_b, (size_t)smem_max, s);
-        }
     }
     const size_t mu_b = P.do_assign ? (size_t)P.pt * P.Kpad * 4 : 0;
     // the incremental mode touches only rows whose label changed (few after the
