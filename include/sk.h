@@ -277,6 +277,87 @@ sk_status sk_mean_accumulate(const sk_ctx *ctx, const int32_t *idx, const float 
 sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_total,
                            double *mean, void *stream);
 
+/* ---- Many data sets, one launch per stage (no paper counterpart: the
+ * paper's method applied to a batch of independent data sets).
+ *
+ * Each item describes one data set with its own p, m, seed and K and the
+ * device buffers of every stage: raw rows X (n x p, leading dimension ldx,
+ * global row offset row0), ELL output idx / val (n x m), Gram accumulator G
+ * (pt x pt float64) with its workspace gram_work (sk_cov_workspace_bytes of a
+ * handle of the same p, m for `gram_mode` and n rows), and the K-means state
+ * mu (K x pt float32), labels (n int32), S (K x pt float64), cnt (K x pt
+ * int32), nk (K int64) and changed (one int64 or NULL).  All device buffers
+ * are caller-owned and must stay valid while the batch is used.
+ *
+ * Supported items: 4 <= p (pt >= 256 for the Gram: one tile shape per
+ * launch), p % 4 == 0, ldx % 4 == 0 and X 16-byte aligned (rows staged with
+ * bulk copies), 1 <= K <= 64.  Other items are rejected by sk_batch_create
+ * with SK_EUNSUPPORTED or SK_EINVAL. */
+typedef struct sk_batch_item {
+    int64_t p, m;
+    uint64_t seed;
+    uint32_t flags;
+    const float *X;
+    int64_t n, ldx, row0;
+    int32_t *idx;
+    float *val;
+    double *G;
+    void *gram_work;
+    int64_t gram_work_bytes;
+    int32_t K;
+    float *mu;
+    int32_t *labels;
+    double *S;
+    int32_t *cnt;
+    int64_t *nk;
+    int64_t *changed;
+} sk_batch_item;
+
+/* Opaque host-side plan of a batch: per data set launch parameters and the
+ * task lists of the persistent kernels.  Holds no device memory. */
+typedef struct sk_batch sk_batch;
+
+/* Validates nd items (host array, copied) and builds the plan for the Gram
+ * precision mode gram_mode (SK_GRAM_BF16 or SK_GRAM_BF16X3).  Needs the
+ * current CUDA device (launch attributes are set here).  *b receives the
+ * plan (host memory, freed by sk_batch_destroy). */
+sk_status sk_batch_create(sk_batch **b, const sk_batch_item *items, int32_t nd,
+                          int32_t gram_mode);
+
+/* Device bytes of the plan's tables (for sk_batch_upload); -1 for NULL. */
+int64_t sk_batch_workspace_bytes(const sk_batch *b);
+
+/* Copies the plan's tables into `work` (device, at least
+ * sk_batch_workspace_bytes bytes, 256-byte aligned) on the stream; the calls
+ * below read them there, so `work` must stay valid and untouched while the
+ * batch is used.  Call it outside stream capture; the calls below may be
+ * captured. */
+sk_status sk_batch_upload(sk_batch *b, void *work, int64_t work_bytes, void *stream);
+
+/* sk_compress of every data set in one persistent launch. */
+sk_status sk_batch_compress(const sk_batch *b, void *stream);
+
+/* sk_cov_reset of every data set's G (one memset each). */
+sk_status sk_batch_cov_reset(const sk_batch *b, void *stream);
+
+/* sk_cov_accumulate of every data set in one launch of the bucketing pass
+ * and one launch of the tensor-core Gram. */
+sk_status sk_batch_cov_accumulate(const sk_batch *b, void *stream);
+
+/* Zeroes every data set's S, cnt, nk in one launch. */
+sk_status sk_batch_kmeans_reset(const sk_batch *b, void *stream);
+
+/* One K-means pass over every data set in one persistent launch:
+ * incremental = 0 as sk_kmeans_step (after sk_batch_kmeans_reset),
+ * incremental = 1 as sk_kmeans_step_delta. */
+sk_status sk_batch_kmeans_step(const sk_batch *b, int32_t incremental, void *stream);
+
+/* sk_kmeans_finalize of every data set in one launch. */
+sk_status sk_batch_kmeans_finalize(const sk_batch *b, void *stream);
+
+/* Frees a plan (NULL is ignored). */
+void sk_batch_destroy(sk_batch *b);
+
 /* Reports SK_ETIMEOUT if a bounded device wait of this library ran out since
  * the last call (and clears the flag), SK_ECUDA on a pending CUDA error, else
  * SK_OK.  Synchronises the given stream first. */

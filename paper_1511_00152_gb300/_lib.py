@@ -75,6 +75,16 @@ def load(path: str | None = None):
             "sk_kmeans2_finalize": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_mean_accumulate": (st, [vp, vp, vp, i64, vp, vp]),
             "sk_mean_finalize": (st, [vp, vp, i64, vp, vp]),
+            "sk_batch_create": (st, [ctypes.POINTER(vp), vp, i32, i32]),
+            "sk_batch_workspace_bytes": (i64, [vp]),
+            "sk_batch_upload": (st, [vp, vp, i64, vp]),
+            "sk_batch_compress": (st, [vp, vp]),
+            "sk_batch_cov_reset": (st, [vp, vp]),
+            "sk_batch_cov_accumulate": (st, [vp, vp]),
+            "sk_batch_kmeans_reset": (st, [vp, vp]),
+            "sk_batch_kmeans_step": (st, [vp, i32, vp]),
+            "sk_batch_kmeans_finalize": (st, [vp, vp]),
+            "sk_batch_destroy": (None, [vp]),
             "sk_device_status": (st, [vp]),
             "sk_last_error": (ctypes.c_char_p, []),
         }
@@ -386,6 +396,87 @@ def sk_mean_finalize(ctx: Ctx, sums, n_total: int, mean=None, stream=None):
     _check("sk_mean_finalize", load().sk_mean_finalize(ctx.handle, _ptr(sums), int(n_total),
                                                        _ptr(mean), _stream(stream)))
     return mean
+
+
+class SkBatchItem(ctypes.Structure):
+    """sk_batch_item of include/sk.h (same field order and types)."""
+    _fields_ = [("p", ctypes.c_int64), ("m", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("X", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("ldx", ctypes.c_int64), ("row0", ctypes.c_int64), ("idx", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("G", ctypes.c_void_p), ("gram_work", ctypes.c_void_p),
+                ("gram_work_bytes", ctypes.c_int64), ("K", ctypes.c_int32), ("mu", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("S", ctypes.c_void_p), ("cnt", ctypes.c_void_p),
+                ("nk", ctypes.c_void_p), ("changed", ctypes.c_void_p)]
+
+
+class Batch:
+    """Owns an sk_batch* (host plan) and keeps the item tensors alive."""
+
+    def __init__(self, handle: int, keep):
+        self._h = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.sk_batch_destroy(self._h)
+                self._h = ctypes.c_void_p(0)
+        except Exception:
+            pass
+
+
+def sk_batch_create(items, gram_mode: int, keep=None) -> Batch:
+    """items: list of SkBatchItem (device pointers filled in by the caller)."""
+    arr = (SkBatchItem * len(items))(*items)
+    h = ctypes.c_void_p(0)
+    _check("sk_batch_create", load().sk_batch_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p),
+                                                     len(items), int(gram_mode)))
+    return Batch(h.value, keep)
+
+
+def sk_batch_workspace_bytes(b: Batch) -> int:
+    return int(load().sk_batch_workspace_bytes(b.handle))
+
+
+def sk_batch_upload(b: Batch, work, stream=None):
+    _check("sk_batch_upload", load().sk_batch_upload(b.handle, _ptr(work),
+                                                     work.numel() * work.element_size(),
+                                                     _stream(stream)))
+
+
+def sk_batch_compress(b: Batch, stream=None):
+    _check("sk_batch_compress", load().sk_batch_compress(b.handle, _stream(stream)))
+
+
+def sk_batch_cov_reset(b: Batch, stream=None):
+    _check("sk_batch_cov_reset", load().sk_batch_cov_reset(b.handle, _stream(stream)))
+
+
+def sk_batch_cov_accumulate(b: Batch, stream=None):
+    _check("sk_batch_cov_accumulate", load().sk_batch_cov_accumulate(b.handle, _stream(stream)))
+
+
+def sk_batch_kmeans_reset(b: Batch, stream=None):
+    _check("sk_batch_kmeans_reset", load().sk_batch_kmeans_reset(b.handle, _stream(stream)))
+
+
+def sk_batch_kmeans_step(b: Batch, incremental: bool, stream=None):
+    _check("sk_batch_kmeans_step", load().sk_batch_kmeans_step(b.handle, 1 if incremental else 0,
+                                                               _stream(stream)))
+
+
+def sk_batch_kmeans_finalize(b: Batch, stream=None):
+    _check("sk_batch_kmeans_finalize", load().sk_batch_kmeans_finalize(b.handle, _stream(stream)))
+
+
+def sk_batch_destroy(b: Batch):
+    if b._h:
+        load().sk_batch_destroy(b._h)
+        b._h = ctypes.c_void_p(0)
 
 
 def sk_device_status(stream=None) -> int:

@@ -18,6 +18,10 @@
 // step, which is either an earlier step's displaced value (found with
 // __match_any_sync) or the position's state after the earlier chunks (a
 // tagged shared-memory array).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -38,9 +42,18 @@ struct CompressParams {
     int vec;
     int mix;            // 0: no preconditioning (H = D = I), the ablation of Sec. VII
     unsigned int *err;  // device error word (bounded waits)
+    int ctas_per_sm;    // autotuned residency cap (0: as many as fit)
 };
 
 constexpr int kNB = 2;  // staging buffers per warp (one unit in flight ahead)
+
+// One task of the multi-data-set launch: units [u_begin, u_end) of data set d.
+struct CompressTask {
+    int32_t d;
+    int32_t L;
+    int64_t u_begin;
+    int64_t u_end;
+};
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -264,27 +277,57 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
     }
 }
 
+// Shared-memory layout: the fixed part first (mbarriers, then each warp's
+// mask-word window), so that the persistent multi-dataset kernel can run
+// units of different pt back to back on the same barriers; then, per row
+// group, the staging buffers, the virtual Fisher-Yates array and the hit table.
+constexpr size_t kFixedSmem = (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4;
+
+template <int L, bool TMA>
+constexpr size_t compress_smem_bytes() {
+    constexpr int PT = 1 << L;
+    constexpr int G = (L > 10) ? (PT >> 10) : 1;
+    constexpr int NG = kWarps / G;
+    constexpr int BUF = (L <= 10) ? 1024 : PT;
+    constexpr int NBUF = TMA ? kNB : 1;
+    return kFixedSmem + (size_t)NG * NBUF * BUF * 4 + (size_t)NG * PT * 4 + (size_t)NG * 32 * 4;
+}
+
+__device__ __forceinline__ void init_unit_barriers(unsigned char *smem_raw) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw) + warp * kNB;
+    if (lane == 0)
+        for (int b = 0; b < kNB; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+}
+
+// One CTA processes units u = u0 + grp + k * stride (u < u_end) of the data
+// set described by P: a unit is RPU rows (pt <= 1024, one warp each) or one
+// row (pt > 1024, G warps).  kloc counts the units this warp has staged
+// through its two TMA buffers (it carries the buffer / barrier-phase
+// sequence across calls).  Returns false if a bounded wait ran out.
 template <int L, bool DENSE, bool TMA>
-__global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams P) {
+__device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t u0,
+                                               int64_t stride, int64_t u_end,
+                                               unsigned char *smem_raw, int64_t &kloc) {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;  // warps per row group
     constexpr int NG = kWarps / G;                // row groups per CTA
     constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
     constexpr int BUF = (L <= 10) ? 1024 : PT;
     constexpr int NBUF = TMA ? kNB : 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = warp / G, wg = warp % G;
-    float *ybufs = reinterpret_cast<float *>(smem_raw) + grp * NBUF * BUF;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw) + warp * kNB;
+    uint32_t *words = reinterpret_cast<uint32_t *>(smem_raw + (size_t)kWarps * kNB * 8) + warp * 256;
+    unsigned char *var = smem_raw + kFixedSmem;
+    float *ybufs = reinterpret_cast<float *>(var) + grp * NBUF * BUF;
     float *ybuf = ybufs;
-    unsigned char *after = smem_raw + (size_t)NG * NBUF * BUF * 4;
+    unsigned char *after = var + (size_t)NG * NBUF * BUF * 4;
     uint32_t *A = reinterpret_cast<uint32_t *>(after) + grp * PT;
     uint32_t *hit = reinterpret_cast<uint32_t *>(after + (size_t)NG * PT * 4) + grp * 32;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(after + (size_t)NG * PT * 4 + NG * 32 * 4) +
-                     warp * kNB;
-    uint32_t *words = reinterpret_cast<uint32_t *>(after + (size_t)NG * PT * 4 + NG * 32 * 4 +
-                                                   (size_t)kWarps * kNB * 8) +
-                      warp * 256;
 
     if constexpr (!DENSE) {
         if (wg == 0)
@@ -301,19 +344,19 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
         smask |= sign_bit(P.k0, P.k1, (uint32_t)c) << r;
     }
 
-    const int64_t nunits = (L <= 10) ? (P.n + RPU - 1) / RPU : P.n;
-    const int64_t stride = (int64_t)gridDim.x * NG;
-    const int64_t u_first = (int64_t)blockIdx.x * NG + grp;
+    const int64_t nunits = u_end;
+    const int64_t u_first = u0 + grp;
+    bool ok = true;
     if constexpr (TMA) {
-        if (lane == 0)
-            for (int b = 0; b < kNB; ++b)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + b)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        __syncwarp();
-        if (u_first < nunits)
-            issue_unit<L>(P, u_first, wg, ybufs + ((L > 10) ? 1024 * wg : 0), smem_u32(mbar), lane);
+        // the buffer may have been read by the previous call's gathers
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        group_sync<G>(grp);
+        if (u_first < nunits) {
+            const int b0 = (int)(kloc & 1);
+            issue_unit<L>(P, u_first, wg, ybufs + b0 * BUF + ((L > 10) ? 1024 * wg : 0),
+                          smem_u32(mbar + b0), lane);
+        }
     }
-    int64_t kloc = 0;  // units processed by this group
     for (int64_t u = u_first; u < nunits; u += stride, ++kloc) {
         const int64_t r0 = u * RPU;
         float v[32];
@@ -329,7 +372,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
             if (!mbar_wait_bounded(smem_u32(mbar + bsel), (uint32_t)((kloc >> 1) & 1))) {
                 if (lane == 0 && P.err) atomicOr(P.err, 2u);
                 // wait (bounded) for the copy still in flight, then stop
-                mbar_wait_bounded(smem_u32(mbar + (bsel ^ 1)), (uint32_t)(((kloc + 1) >> 1) & 1));
+                if (u + stride < nunits)
+                    mbar_wait_bounded(smem_u32(mbar + (bsel ^ 1)), (uint32_t)(((kloc + 1) >> 1) & 1));
+                ok = false;
                 break;
             }
             float *wb = ybuf + ((L > 10) ? 1024 * wg : 0);
@@ -484,6 +529,21 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
             }
         }
     }
+    return ok;
+}
+
+template <int L, bool DENSE, bool TMA>
+__global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams P) {
+    constexpr int PT = 1 << L;
+    constexpr int G = (L > 10) ? (PT >> 10) : 1;
+    constexpr int NG = kWarps / G;
+    constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (TMA) init_unit_barriers(smem_raw);
+    const int64_t nunits = (L <= 10) ? (P.n + RPU - 1) / RPU : P.n;
+    int64_t kloc = 0;
+    compress_units<L, DENSE, TMA>(P, (int64_t)blockIdx.x * NG, (int64_t)gridDim.x * NG, nunits,
+                                  smem_raw, kloc);
 }
 
 template <int L, bool DENSE, bool TMA>
@@ -492,10 +552,7 @@ cudaError_t launch_LT(const CompressParams &P, cudaStream_t s) {
     constexpr int G = (L > 10) ? (PT >> 10) : 1;
     constexpr int NG = kWarps / G;
     constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
-    constexpr int BUF = (L <= 10) ? 1024 : PT;
-    constexpr int NBUF = TMA ? kNB : 1;
-    const size_t smem = (size_t)NG * NBUF * BUF * 4 + (size_t)NG * PT * 4 + NG * 32 * 4 +
-                        (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4;
+    const size_t smem = compress_smem_bytes<L, TMA>();
     auto kern = compress_kernel<L, DENSE, TMA>;
     cudaError_t e0 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);
@@ -507,6 +564,7 @@ cudaError_t launch_LT(const CompressParams &P, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     const int64_t nunits = (L <= 10) ? (P.n + RPU - 1) / RPU : P.n;
     int64_t blocks = (nunits + NG - 1) / NG;
+    if (P.ctas_per_sm > 0 && P.ctas_per_sm < per_sm) per_sm = P.ctas_per_sm;
     const int64_t cap = (int64_t)sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
@@ -544,11 +602,77 @@ cudaError_t dispatch(int L, const CompressParams &P, cudaStream_t s) {
     }
 }
 
+// ---- many data sets in one persistent launch
+//
+// The work is a list of tasks (data set, unit range) of about the same
+// number of bytes; persistent CTAs take tasks in order from a ticket counter
+// and run them with the pt-specific unit code (TMA staging only: every data
+// set has 16-byte aligned rows).  Between tasks the CTA synchronises, so the
+// shared memory of one task's layout is free before the next one's.
+__global__ void __launch_bounds__(kWarps * 32, 2) compress_batch_kernel(
+    const CompressParams *Ps, const CompressTask *tasks, int ntasks, unsigned int *ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_task;
+    init_unit_barriers(smem_raw);
+    int64_t kloc = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= ntasks) break;
+        const CompressTask T = tasks[t];
+        const CompressParams P = Ps[T.d];
+        bool ok = true;
+        switch (T.L) {
+#define SK_BATCH_CASE(LL)                                                                        \
+    case LL:                                                                                     \
+        ok = compress_units<LL, false, true>(P, T.u_begin, kWarps / ((LL > 10) ? (1 << (LL - 10)) \
+                                                                                : 1),            \
+                                             T.u_end, smem_raw, kloc);                          \
+        break;
+            SK_BATCH_CASE(2)
+            SK_BATCH_CASE(3)
+            SK_BATCH_CASE(4)
+            SK_BATCH_CASE(5)
+            SK_BATCH_CASE(6)
+            SK_BATCH_CASE(7)
+            SK_BATCH_CASE(8)
+            SK_BATCH_CASE(9)
+            SK_BATCH_CASE(10)
+            SK_BATCH_CASE(11)
+            SK_BATCH_CASE(12)
+            SK_BATCH_CASE(13)
+#undef SK_BATCH_CASE
+            default:
+                break;
+        }
+        // every group is done with this task's shared memory (and has read
+        // s_task) before the next task starts
+        if (__syncthreads_or(!ok)) break;
+    }
+}
+
+size_t compress_smem_for(int L) {
+    switch (L) {
+        case 2: return compress_smem_bytes<2, true>();
+        case 3: return compress_smem_bytes<3, true>();
+        case 4: return compress_smem_bytes<4, true>();
+        case 5: return compress_smem_bytes<5, true>();
+        case 6: return compress_smem_bytes<6, true>();
+        case 7: return compress_smem_bytes<7, true>();
+        case 8: return compress_smem_bytes<8, true>();
+        case 9: return compress_smem_bytes<9, true>();
+        case 10: return compress_smem_bytes<10, true>();
+        case 11: return compress_smem_bytes<11, true>();
+        case 12: return compress_smem_bytes<12, true>();
+        default: return compress_smem_bytes<13, true>();
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
-                            int64_t row0, int32_t *idx, float *val, float *Y,
-                            cudaStream_t s) {
+static CompressParams make_params(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                                  int64_t row0, int32_t *idx, float *val, float *Y) {
     CompressParams P;
     P.X = X;
     P.n = n;
@@ -565,7 +689,91 @@ cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t 
     P.scale = P.mix ? (float)(1.0 / sqrt((double)c.pt)) : 1.0f;
     P.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (c.p % 4 == 0) && (ldx % 4 == 0);
     P.err = device_error_word();
+    P.ctas_per_sm = c.compress_ctas;
+    return P;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool compress_batchable(const sk_ctx &c, const float *X, int64_t ldx) {
+    return c.log2pt >= 2 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (c.p % 4 == 0) &&
+           (ldx % 4 == 0);
+}
+
+cudaError_t compress_batch_build(const sk_ctx *ctxs, const BatchRows *rows, int nd,
+                                 int units_per_group, std::vector<unsigned char> &table,
+                                 CompressBatchInfo &info) {
+    std::vector<CompressParams> Ps((size_t)nd);
+    std::vector<CompressTask> tasks;
+    int Lmax = 2;
+    for (int d = 0; d < nd; ++d) {
+        const sk_ctx &c = ctxs[d];
+        Ps[d] = make_params(c, rows[d].X, rows[d].n, rows[d].ldx, rows[d].row0, rows[d].idx,
+                            rows[d].val, nullptr);
+        const int L = c.log2pt;
+        if (L > Lmax) Lmax = L;
+        const int64_t rpu = (L <= 10) ? (1024 >> L) : 1;
+        const int64_t ng = kWarps / ((L > 10) ? (1 << (L - 10)) : 1);
+        const int64_t nunits = (L <= 10) ? (rows[d].n + rpu - 1) / rpu : rows[d].n;
+        const int64_t per = ng * (int64_t)units_per_group;
+        for (int64_t u = 0; u < nunits; u += per) {
+            CompressTask T;
+            T.d = d;
+            T.L = L;
+            T.u_begin = u;
+            T.u_end = (u + per < nunits) ? u + per : nunits;
+            tasks.push_back(T);
+        }
+    }
+    // largest tasks (pt) first: the tail of the launch is made of small ones
+    std::stable_sort(tasks.begin(), tasks.end(),
+                     [](const CompressTask &a, const CompressTask &b) { return a.L > b.L; });
+    size_t smem = 0;
+    for (int d = 0; d < nd; ++d) {
+        const size_t b = compress_smem_for(ctxs[d].log2pt);
+        if (b > smem) smem = b;
+    }
+    info.smem = smem;
+    info.ntasks = (int)tasks.size();
+    info.params_off = align256(table.size());
+    info.tasks_off = align256(info.params_off + Ps.size() * sizeof(CompressParams));
+    info.ticket_off = align256(info.tasks_off + tasks.size() * sizeof(CompressTask));
+    table.resize(info.ticket_off + 256, 0);
+    std::memcpy(table.data() + info.params_off, Ps.data(), Ps.size() * sizeof(CompressParams));
+    if (!tasks.empty())
+        std::memcpy(table.data() + info.tasks_off, tasks.data(), tasks.size() * sizeof(CompressTask));
+    cudaError_t e = cudaFuncSetAttribute(compress_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compress_batch_kernel, kWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > info.ntasks) grid = info.ntasks > 0 ? info.ntasks : 1;
+    info.grid = (int)grid;
+    (void)Lmax;
+    return cudaSuccess;
+}
+
+cudaError_t compress_batch_launch(const CompressBatchInfo &info, unsigned char *dev_table,
+                                  cudaStream_t s) {
+    if (info.ntasks == 0) return cudaSuccess;
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(dev_table + info.ticket_off);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    compress_batch_kernel<<<(unsigned)info.grid, kWarps * 32, info.smem, s>>>(
+        reinterpret_cast<const CompressParams *>(dev_table + info.params_off),
+        reinterpret_cast<const CompressTask *>(dev_table + info.tasks_off), info.ntasks, ticket);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                            int64_t row0, int32_t *idx, float *val, float *Y,
+                            cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    const CompressParams P = make_params(c, X, n, ldx, row0, idx, val, Y);
     return Y ? dispatch<true>(c.log2pt, P, s) : dispatch<false>(c.log2pt, P, s);
 }
 

@@ -24,6 +24,9 @@
 // frees TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <cstring>
+#include <vector>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -160,12 +163,19 @@ __device__ __forceinline__ uint32_t sw_off(int r, int k) {
 // (column-in-block, row-in-slab) element in a K-major, 128B-swizzled operand
 // tile, so the Gram producers only copy.  One CTA per slab; the per-block
 // counters take warp-aggregated shared-memory atomics.
-__global__ void __launch_bounds__(256) bucket_kernel(const int32_t *idx, const float *val,
-                                                     int64_t n, int m, int pt, int nblk,
-                                                     int2 *bkt, int *boff) {
+struct BucketParams {
+    const int32_t *idx;
+    const float *val;
+    int64_t n;
+    int m, pt, nblk;
+    int2 *bkt;
+    int *boff;
+};
+
+__device__ __forceinline__ void bucket_body(const int32_t *idx, const float *val, int64_t n, int m,
+                                            int pt, int nblk, int2 *bkt, int *boff, int64_t s) {
     __shared__ int hist[64];
     __shared__ int cursor[64];
-    const int64_t s = blockIdx.x;
     const int64_t r0 = s * kSlab;
     const int rows = (int)((n - r0) < kSlab ? (n - r0) : kSlab);
     const int total = rows * m;
@@ -217,6 +227,25 @@ __global__ void __launch_bounds__(256) bucket_kernel(const int32_t *idx, const f
     }
 }
 
+__global__ void __launch_bounds__(256) bucket_kernel(const int32_t *idx, const float *val,
+                                                     int64_t n, int m, int pt, int nblk,
+                                                     int2 *bkt, int *boff) {
+    bucket_body(idx, val, n, m, pt, nblk, bkt, boff, blockIdx.x);
+}
+
+// Many data sets: CTA b works on slab b - start[d] of the data set d with
+// start[d] <= b < start[d + 1].
+__global__ void __launch_bounds__(256) bucket_batch_kernel(const BucketParams *Bs, const int *start,
+                                                           int nd) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const BucketParams B = Bs[lo];
+    bucket_body(B.idx, B.val, B.n, B.m, B.pt, B.nblk, B.bkt, B.boff, (int64_t)blockIdx.x - start[lo]);
+}
+
 __device__ __forceinline__ void decode_tile(const TcParams &P, int t, int &bi, int &bj) {
     const int ratio = P.N / kTileM;  // column blocks are ratio row blocks wide
     bi = 0;
@@ -232,7 +261,7 @@ __device__ __forceinline__ void decode_tile(const TcParams &P, int t, int &bi, i
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
+__device__ __forceinline__ void gram_tc_body(const TcParams &P, int bid) {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     // 1024-byte alignment of the operand tiles (the swizzle pattern repeats per 1 KB)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -250,8 +279,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x % P.ntiles;
-    const int split = blockIdx.x / P.ntiles;
+    const int tile = bid % P.ntiles;
+    const int split = bid / P.ntiles;
     int bi, bj;
     decode_tile(P, tile, bi, bj);
     const int I0 = bi * kTileM, J0 = bj * P.N;
@@ -552,6 +581,24 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
     }
 }
 
+__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(TcParams P) {
+    gram_tc_body(P, blockIdx.x);
+}
+
+// Many data sets in one launch: CTA b runs unit b - start[d] (tile and row
+// split) of data set d with start[d] <= b < start[d + 1]; all data sets share
+// the tile width, the precision mode and the ring layout.
+__global__ void __launch_bounds__(kThreads, 1) gram_tc_batch_kernel(const TcParams *Ps,
+                                                                   const int *start, int nd) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const TcParams P = Ps[lo];
+    gram_tc_body(P, (int)blockIdx.x - start[lo]);
+}
+
 }  // namespace
 
 int64_t gram_tc_workspace(const sk_ctx &c, int64_t n) {
@@ -563,17 +610,19 @@ int64_t gram_tc_workspace(const sk_ctx &c, int64_t n) {
     return ((ent + 255) & ~int64_t(255)) + offs + 256;
 }
 
-cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const float *val,
-                           int64_t n, double *G, void *work, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
+// Launch configuration of one data set's Gram (no launch): tile shape,
+// precision stages, row splits, ring slot size and the workspace carve.
+static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const float *val,
+                           int64_t n, double *G, void *work, TcParams &P, size_t &smem,
+                           int64_t &nslab) {
     if (c.pt < kTileM) return cudaErrorInvalidValue;
-    TcParams P;
     P.idx = idx;
     P.val = val;
     P.n = n;
     P.m = (int)c.m;
     P.pt = (int)c.pt;
     P.N = c.pt >= 256 ? 256 : (int)c.pt;
+    if (c.gram_n == 128 && c.pt >= 128) P.N = 128;  // autotuned tile width
     P.nbi = P.pt / kTileM;
     P.nbj = P.pt / P.N;
     const int ratio = P.N / kTileM;
@@ -587,22 +636,18 @@ cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const 
     P.G = G;
     P.nblk = P.pt / kBlk;
     // workspace: bucketed entries (8 bytes each, 64 m per slab), then offsets
-    const int64_t nslab = (n + kSlab - 1) / kSlab;
+    nslab = (n + kSlab - 1) / kSlab;
     const int64_t ent = nslab * kSlab * c.m * (int64_t)sizeof(int2);
     unsigned char *w = static_cast<unsigned char *>(work);
     P.bkt = reinterpret_cast<const int2 *>(w);
     P.boff = reinterpret_cast<const int *>(w + ((ent + 255) & ~int64_t(255)));
-    bucket_kernel<<<(unsigned)nslab, 256, 0, s>>>(idx, val, n, P.m, P.pt, P.nblk,
-                                                  reinterpret_cast<int2 *>(w),
-                                                  const_cast<int *>(P.boff));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // row splits: no segment longer than kSegmentRows; among the counts that
     // allow, take the one whose units fill whole waves of the SMs best
+    // (times the autotuned multiplier)
     const int64_t min_splits = (n + kSegmentRows - 1) / kSegmentRows;
     int64_t best = min_splits;
     double best_eff = 0.0;
@@ -617,6 +662,10 @@ cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const 
         }
         if (eff > 0.95) break;
     }
+    if (c.split_mult > 1) {
+        const int64_t cap = (n + kSlab - 1) / kSlab;
+        best = best * c.split_mult < cap ? best * c.split_mult : cap;
+    }
     int64_t rps = (n + best - 1) / best;
     rps = (rps + kSlab - 1) / kSlab * kSlab;
     P.rows_per_split = rps;
@@ -629,11 +678,97 @@ cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const 
     if (slot > 65536) slot = 65536;
     if (slot < 16) return cudaErrorInvalidConfiguration;
     P.slot_bytes = (int)slot;
-    const size_t smem = fixed + (size_t)kRing * P.slot_bytes;
+    smem = fixed + (size_t)kRing * P.slot_bytes;
+    return cudaSuccess;
+}
+
+cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx, const float *val,
+                           int64_t n, double *G, void *work, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    TcParams P;
+    size_t smem = 0;
+    int64_t nslab = 0;
+    cudaError_t e = tc_plan(c, mode, idx, val, n, G, work, P, smem, nslab);
+    if (e != cudaSuccess) return e;
+    bucket_kernel<<<(unsigned)nslab, 256, 0, s>>>(idx, val, n, P.m, P.pt, P.nblk,
+                                                  const_cast<int2 *>(P.bkt),
+                                                  const_cast<int *>(P.boff));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)P.ntiles * P.nsplits;
     gram_tc_kernel<<<(unsigned)grid, kThreads, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+cudaError_t gram_batch_build(const sk_ctx *ctxs, const BatchGram *rows, int nd, int mode,
+                             std::vector<unsigned char> &table, GramBatchInfo &info) {
+    std::vector<TcParams> Ps((size_t)nd);
+    std::vector<BucketParams> Bs((size_t)nd);
+    std::vector<int> slab_start((size_t)nd + 1), cta_start((size_t)nd + 1);
+    int64_t slabs = 0, ctas = 0;
+    size_t smem = 0;
+    for (int d = 0; d < nd; ++d) {
+        TcParams &P = Ps[d];
+        size_t sm = 0;
+        int64_t nslab = 0;
+        slab_start[d] = (int)slabs;
+        cta_start[d] = (int)ctas;
+        if (rows[d].n == 0) {
+            std::memset(&P, 0, sizeof(P));
+            std::memset(&Bs[d], 0, sizeof(BucketParams));
+            continue;
+        }
+        cudaError_t e = tc_plan(ctxs[d], mode, rows[d].idx, rows[d].val, rows[d].n, rows[d].G,
+                                rows[d].work, P, sm, nslab);
+        if (e != cudaSuccess) return e;
+        if (smem && (P.N != Ps[info.first].N || P.nstages != Ps[info.first].nstages ||
+                     P.slot_bytes != Ps[info.first].slot_bytes))
+            return cudaErrorInvalidValue;  // one launch needs one tile shape
+        if (!smem) info.first = d;
+        smem = sm;
+        Bs[d] = BucketParams{rows[d].idx, rows[d].val, rows[d].n, P.m, P.pt, P.nblk,
+                             const_cast<int2 *>(P.bkt), const_cast<int *>(P.boff)};
+        slabs += nslab;
+        ctas += (int64_t)P.ntiles * P.nsplits;
+        if (slabs > 0x7fffffff || ctas > 0x7fffffff) return cudaErrorInvalidValue;
+    }
+    slab_start[nd] = (int)slabs;
+    cta_start[nd] = (int)ctas;
+    info.nd = nd;
+    info.slabs = slabs;
+    info.ctas = ctas;
+    info.smem = smem;
+    info.tc_off = al256(table.size());
+    info.bk_off = al256(info.tc_off + Ps.size() * sizeof(TcParams));
+    info.slab_off = al256(info.bk_off + Bs.size() * sizeof(BucketParams));
+    info.cta_off = al256(info.slab_off + slab_start.size() * sizeof(int));
+    table.resize(al256(info.cta_off + cta_start.size() * sizeof(int)), 0);
+    std::memcpy(table.data() + info.tc_off, Ps.data(), Ps.size() * sizeof(TcParams));
+    std::memcpy(table.data() + info.bk_off, Bs.data(), Bs.size() * sizeof(BucketParams));
+    std::memcpy(table.data() + info.slab_off, slab_start.data(), slab_start.size() * sizeof(int));
+    std::memcpy(table.data() + info.cta_off, cta_start.data(), cta_start.size() * sizeof(int));
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_batch_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t gram_batch_launch(const GramBatchInfo &info, unsigned char *dev_table, cudaStream_t s) {
+    if (info.ctas == 0) return cudaSuccess;
+    bucket_batch_kernel<<<(unsigned)info.slabs, 256, 0, s>>>(
+        reinterpret_cast<const BucketParams *>(dev_table + info.bk_off),
+        reinterpret_cast<const int *>(dev_table + info.slab_off), info.nd);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_tc_batch_kernel<<<(unsigned)info.ctas, kThreads, info.smem, s>>>(
+        reinterpret_cast<const TcParams *>(dev_table + info.tc_off),
+        reinterpret_cast<const int *>(dev_table + info.cta_off), info.nd);
     return cudaGetLastError();
 }
 

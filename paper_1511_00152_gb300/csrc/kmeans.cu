@@ -21,6 +21,10 @@
 // Update: in the same pass, each (row, t) entry adds val to S[label][idx] and
 // 1 to cnt[label][idx] in CTA-private shared-memory accumulators, flushed to
 // the caller's float64 / int32 sums with one atomic per touched entry.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -73,44 +77,16 @@ __device__ __forceinline__ int slot_of_lane(const KmParams &P, int l) {
     return P.G ? (l >> 4) * P.G + (l & 15) / P.LPR : l / P.LPR;
 }
 
+// The rows of one pass set: warp w handles the RW-row groups starting at
+// base0 (its first) and every step rows after, below r_end.  mus / sS, sC,
+// snk / stage_all are the shared-memory centre table, update sums and row
+// staging (each used only by the variants that have them).
 template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE, bool COPIES>
-__global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
+__device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus, float *sS,
+                                            int32_t *sC, int32_t *snk, int2 *stage_all,
+                                            int64_t base0, int64_t step, int64_t r_end) {
     constexpr int NP = KPL / 2;  // packed pairs per lane
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t off = 0;
-    float *mus = reinterpret_cast<float *>(smem_raw + off);
-    if (MU_SMEM && P.do_assign) off += (size_t)P.pt * (COPIES ? 32 : P.Kpad) * 4;
-    float *sS = reinterpret_cast<float *>(smem_raw + off);
-    int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
-    int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
-    if (PRIV && P.do_update == 1) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
-    int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + off);
-
     const int tid = threadIdx.x;
-    const int KP = P.K * P.pt;
-    if (MU_SMEM && P.do_assign) {
-        if constexpr (COPIES) {
-            for (int e = tid; e < P.pt * 32; e += blockDim.x) {
-                const int j = e >> 5, w = e & 31;
-                const int c = w / P.Kpad, k = w - c * P.Kpad;
-                mus[e] = (c < P.G && k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
-            }
-        } else {
-            for (int e = tid; e < P.pt * P.Kpad; e += blockDim.x) {
-                const int j = e / P.Kpad, k = e - j * P.Kpad;
-                mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
-            }
-        }
-    }
-    if (PRIV && P.do_update == 1) {
-        for (int e = tid; e < KP; e += blockDim.x) {
-            sS[e] = 0.f;
-            sC[e] = 0;
-        }
-        for (int e = tid; e < P.K; e += blockDim.x) snk[e] = 0;
-    }
-    __syncthreads();
-
     const int lane = tid & 31, warp = tid >> 5;
     // row slot of this lane in the warp, its centre group, and (per half-warp
     // layout) the slot's position in its half, which selects the copy
@@ -128,13 +104,11 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     }
     const int kbase = kl * KPL;
     int2 *stage = stage_all + (size_t)warp * P.stage_cap;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int m = P.m;
     const int pmask = P.pt - 1;
 
-    for (int64_t base = gwarp * P.RW; base < P.n; base += nwarps * P.RW) {
-        const int rows_here = (int)((P.n - base) < P.RW ? (P.n - base) : P.RW);
+    for (int64_t base = base0; base < r_end; base += step) {
+        const int rows_here = (int)((r_end - base) < P.RW ? (r_end - base) : P.RW);
         if constexpr (STAGE) {
             // this pass's rows are contiguous in the ELL arrays: coalesced copy
             const int total = rows_here * m;
@@ -323,6 +297,51 @@ __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
         }
         if constexpr (STAGE) __syncwarp();  // stage is rewritten by the next pass
     }
+}
+
+template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE, bool COPIES>
+__global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    size_t off = 0;
+    float *mus = reinterpret_cast<float *>(smem_raw + off);
+    if (MU_SMEM && P.do_assign) off += (size_t)P.pt * (COPIES ? 32 : P.Kpad) * 4;
+    float *sS = reinterpret_cast<float *>(smem_raw + off);
+    int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 4);
+    int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + off + (size_t)P.K * P.pt * 8);
+    if (PRIV && P.do_update == 1) off += (size_t)P.K * P.pt * 8 + (((size_t)P.K * 4 + 15) & ~(size_t)15);
+    int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + off);
+
+    const int tid = threadIdx.x;
+    const int KP = P.K * P.pt;
+    if (MU_SMEM && P.do_assign) {
+        if constexpr (COPIES) {
+            for (int e = tid; e < P.pt * 32; e += blockDim.x) {
+                const int j = e >> 5, w = e & 31;
+                const int c = w / P.Kpad, k = w - c * P.Kpad;
+                mus[e] = (c < P.G && k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
+            }
+        } else {
+            for (int e = tid; e < P.pt * P.Kpad; e += blockDim.x) {
+                const int j = e / P.Kpad, k = e - j * P.Kpad;
+                mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
+            }
+        }
+    }
+    if (PRIV && P.do_update == 1) {
+        for (int e = tid; e < KP; e += blockDim.x) {
+            sS[e] = 0.f;
+            sC[e] = 0;
+        }
+        for (int e = tid; e < P.K; e += blockDim.x) snk[e] = 0;
+    }
+    __syncthreads();
+
+    {
+        const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        kmeans_rows<KPL, MU_SMEM, PRIV, STAGE, COPIES>(P, mus, sS, sC, snk, stage_all,
+                                                       gwarp * P.RW, nwarps * P.RW, P.n);
+    }
     if (PRIV && P.do_update == 1) {
         __syncthreads();
         // a slot can carry a nonzero float sum with a zero net count (a row
@@ -345,6 +364,98 @@ __global__ void kmeans_finalize_kernel(int64_t KP, const double *S, const int32_
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = cnt[e];
         if (c > 0) mu[e] = (float)(S[e] / (double)c);
+    }
+}
+
+// ---- many data sets in one persistent launch (K <= 64)
+//
+// Tasks (data set, row range) are taken in order from a ticket counter.  A
+// data set's centres sit in shared memory when they fit the table region
+// (reloaded only when the CTA moves to another data set), and its rows are
+// staged when the per-warp staging fits; otherwise the variant reads them
+// through L1/L2.  Sums go to the caller's float64 / int32 arrays with global
+// atomics (no shared-memory privatisation across data sets).
+struct KmTask {
+    int32_t d;
+    int32_t variant;  // bit 0: centres in shared memory, bit 1: staged rows
+    int64_t r_begin, r_end;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) kmeans_batch_kernel(const KmParams *Ps,
+                                                               const KmTask *tasks, int ntasks,
+                                                               unsigned int *ticket,
+                                                               int mu_cap_bytes, int do_update) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_task, s_last;
+    float *mus = reinterpret_cast<float *>(smem_raw);
+    int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + mu_cap_bytes);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) s_last = -1;
+    for (;;) {
+        if (tid == 0) s_task = (int)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int t = s_task;
+        const int last = s_last;
+        if (t >= ntasks) break;
+        const KmTask T = tasks[t];
+        KmParams P = Ps[T.d];
+        P.do_assign = 1;
+        P.do_update = do_update;
+        if ((T.variant & 1) && T.d != last) {
+            for (int e = tid; e < P.pt * P.Kpad; e += blockDim.x) {
+                const int j = e / P.Kpad, k = e - j * P.Kpad;
+                mus[e] = (k < P.K) ? P.mu[(int64_t)k * P.pt + j] : 0.f;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_last = (T.variant & 1) ? T.d : -1;
+        const int64_t base0 = T.r_begin + (int64_t)warp * P.RW;
+        const int64_t step = (int64_t)kWarpsK * P.RW;
+        switch (T.variant) {
+            case 3:
+                kmeans_rows<2, true, false, true, false>(P, mus, nullptr, nullptr, nullptr,
+                                                         stage_all, base0, step, T.r_end);
+                break;
+            case 1:
+                kmeans_rows<2, true, false, false, false>(P, mus, nullptr, nullptr, nullptr,
+                                                          stage_all, base0, step, T.r_end);
+                break;
+            case 2:
+                kmeans_rows<2, false, false, true, false>(P, mus, nullptr, nullptr, nullptr,
+                                                          stage_all, base0, step, T.r_end);
+                break;
+            default:
+                kmeans_rows<2, false, false, false, false>(P, mus, nullptr, nullptr, nullptr,
+                                                           stage_all, base0, step, T.r_end);
+                break;
+        }
+        // rows done before the centre table, the staging or the ticket is reused
+        __syncthreads();
+    }
+}
+
+// Zero (mode 0) or finalize (mode 1: mu = S / cnt where cnt > 0) the sums of
+// every data set: element e of the concatenated K x pt arrays (start[] is the
+// prefix), plus each data set's nk in mode 0.
+__global__ void kmeans_sums_batch_kernel(const KmParams *Ps, const int64_t *start, int nd,
+                                         int64_t total, int mode) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nd - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const KmParams &P = Ps[lo];
+        const int64_t k = e - start[lo];
+        if (mode == 0) {
+            P.S[k] = 0.0;
+            P.cnt[k] = 0;
+            if (k < P.K) P.nk[k] = 0;
+        } else {
+            const int32_t c = P.cnt[k];
+            if (c > 0) const_cast<float *>(P.mu)[k] = (float)(P.S[k] / (double)c);
+        }
     }
 }
 
@@ -436,6 +547,124 @@ cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
     if (K <= 64) return launch_kpl<2>(P, s);
     if (K <= 128) return launch_kpl<4>(P, s);
     return launch_kpl<8>(P, s);
+}
+
+static size_t km_al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd,
+                               std::vector<unsigned char> &table, KmeansBatchInfo &info) {
+    int dev = 0, smem_max = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<KmParams> Ps((size_t)nd);
+    std::vector<int64_t> start((size_t)nd + 1);
+    // centre-table region: the largest table that fits 70% of shared memory
+    size_t mu_cap = 0;
+    for (int d = 0; d < nd; ++d) {
+        const int LPR = (it[d].K + 1) / 2;
+        const size_t mu_b = (size_t)ctxs[d].pt * (2 * LPR) * 4;
+        if (mu_b <= (size_t)smem_max * 7 / 10 && mu_b > mu_cap) mu_cap = mu_b;
+    }
+    mu_cap = (mu_cap + 15) & ~(size_t)15;
+    const size_t stage_region = (size_t)smem_max - mu_cap;
+    std::vector<KmTask> tasks;
+    int64_t total = 0;
+    size_t stage_used = 0;
+    for (int d = 0; d < nd; ++d) {
+        const sk_ctx &c = ctxs[d];
+        KmParams &P = Ps[d];
+        std::memset(&P, 0, sizeof(P));
+        if (it[d].K < 1 || it[d].K > 64) return cudaErrorInvalidValue;
+        P.idx = it[d].idx;
+        P.val = it[d].val;
+        P.n = it[d].n;
+        P.m = (int)c.m;
+        P.pt = (int)c.pt;
+        P.K = it[d].K;
+        P.LPR = (P.K + 1) / 2;
+        P.Kpad = 2 * P.LPR;
+        P.G = P.LPR <= 16 ? 16 / P.LPR : 0;
+        P.RW = P.G ? 2 * P.G : 32 / P.LPR;
+        P.mu = it[d].mu;
+        P.labels = it[d].labels;
+        P.dist = nullptr;
+        P.S = it[d].S;
+        P.cnt = it[d].cnt;
+        P.nk = it[d].nk;
+        P.changed = reinterpret_cast<unsigned long long *>(it[d].changed);
+        start[d] = total;
+        total += (int64_t)P.K * P.pt;
+        const bool mu_smem = (size_t)P.pt * P.Kpad * 4 <= mu_cap;
+        const size_t st_b = (size_t)kWarpsK * P.RW * P.m * 8;
+        const bool staged = st_b <= stage_region;
+        P.stage_cap = staged ? P.RW * P.m : 0;
+        if (staged && st_b > stage_used) stage_used = st_b;
+        const int variant = (mu_smem ? 1 : 0) | (staged ? 2 : 0);
+        const int64_t per = (int64_t)kWarpsK * P.RW * 16;  // 16 passes per warp
+        for (int64_t r = 0; r < P.n; r += per) {
+            KmTask T;
+            T.d = d;
+            T.variant = variant;
+            T.r_begin = r;
+            T.r_end = (r + per < P.n) ? r + per : P.n;
+            tasks.push_back(T);
+        }
+    }
+    start[nd] = total;
+    // costliest rows (m K) first
+    std::stable_sort(tasks.begin(), tasks.end(), [&](const KmTask &a, const KmTask &b) {
+        return (int64_t)Ps[a.d].m * Ps[a.d].K > (int64_t)Ps[b.d].m * Ps[b.d].K;
+    });
+    info.nd = nd;
+    info.ntasks = (int)tasks.size();
+    info.total = total;
+    info.mu_cap = (int)mu_cap;
+    info.smem = mu_cap + stage_used;
+    info.params_off = km_al256(table.size());
+    info.tasks_off = km_al256(info.params_off + Ps.size() * sizeof(KmParams));
+    info.start_off = km_al256(info.tasks_off + tasks.size() * sizeof(KmTask));
+    info.ticket_off = km_al256(info.start_off + start.size() * sizeof(int64_t));
+    table.resize(info.ticket_off + 256, 0);
+    std::memcpy(table.data() + info.params_off, Ps.data(), Ps.size() * sizeof(KmParams));
+    if (!tasks.empty())
+        std::memcpy(table.data() + info.tasks_off, tasks.data(), tasks.size() * sizeof(KmTask));
+    std::memcpy(table.data() + info.start_off, start.data(), start.size() * sizeof(int64_t));
+    cudaError_t e = cudaFuncSetAttribute(kmeans_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)info.smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeans_batch_kernel, kThreads,
+                                                  info.smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > info.ntasks) grid = info.ntasks > 0 ? info.ntasks : 1;
+    info.grid = (int)grid;
+    return cudaSuccess;
+}
+
+cudaError_t kmeans_batch_launch(const KmeansBatchInfo &info, unsigned char *dev_table, int op,
+                                cudaStream_t s) {
+    const KmParams *Ps = reinterpret_cast<const KmParams *>(dev_table + info.params_off);
+    const int64_t *start = reinterpret_cast<const int64_t *>(dev_table + info.start_off);
+    if (op == 0 || op == 3) {  // reset / finalize
+        if (info.total == 0) return cudaSuccess;
+        int64_t blocks = (info.total + 255) / 256;
+        if (blocks > 8192) blocks = 8192;
+        kmeans_sums_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(Ps, start, info.nd, info.total,
+                                                                 op == 0 ? 0 : 1);
+        return cudaGetLastError();
+    }
+    if (info.ntasks == 0) return cudaSuccess;
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(dev_table + info.ticket_off);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    // op 1: full sums (after a reset), op 2: incremental
+    kmeans_batch_kernel<<<(unsigned)info.grid, kThreads, info.smem, s>>>(
+        Ps, reinterpret_cast<const KmTask *>(dev_table + info.tasks_off), info.ntasks, ticket,
+        info.mu_cap, op == 1 ? 1 : 2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_kmeans_finalize(const sk_ctx &c, int K, const double *S,

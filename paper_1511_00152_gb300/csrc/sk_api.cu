@@ -43,6 +43,12 @@ bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
 
 }  // namespace
 
+namespace sk {
+void set_last_error(const char *msg) {
+    std::snprintf(g_msg, sizeof(g_msg), "%s", msg ? msg : "");
+}
+}  // namespace sk
+
 extern "C" {
 
 sk_status sk_init(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed) {
@@ -72,6 +78,9 @@ sk_status sk_init_ex(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed, uint32_t
     c->m = m;
     c->seed = seed;
     c->flags = flags;
+    c->gram_n = 0;
+    c->split_mult = 0;
+    c->compress_ctas = 0;
     *ctx = c;
     g_msg[0] = 0;
     return SK_OK;

@@ -7,6 +7,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/sk.h"
@@ -108,9 +110,72 @@ struct sk_ctx {
     int64_t m;
     uint64_t seed;
     uint32_t flags;  // SK_FLAG_* of sk_init_ex
+    // autotuned launch choices (0: the built-in heuristics)
+    int gram_n;      // Gram tile width, 128 or 256
+    int split_mult;  // multiplier on the Gram row-split count
+    int compress_ctas;  // compress CTAs per SM (1 or 2)
 };
 
 namespace sk {
+// Records the calling thread's message for sk_last_error (sk_api.cu).
+void set_last_error(const char *msg);
+
+// ---- many data sets in one launch (batch.cu holds the plan; each kernel
+// file builds its part of the device table and launches from it)
+struct BatchRows {  // one data set's rows and ELL output
+    const float *X;
+    int64_t n, ldx, row0;
+    int32_t *idx;
+    float *val;
+};
+struct CompressBatchInfo {
+    size_t params_off, tasks_off, ticket_off, smem;
+    int ntasks, grid;
+};
+bool compress_batchable(const sk_ctx &c, const float *X, int64_t ldx);
+cudaError_t compress_batch_build(const sk_ctx *ctxs, const BatchRows *rows, int nd,
+                                 int units_per_group, std::vector<unsigned char> &table,
+                                 CompressBatchInfo &info);
+cudaError_t compress_batch_launch(const CompressBatchInfo &info, unsigned char *dev_table,
+                                  cudaStream_t s);
+struct BatchGram {  // one data set's ELL rows, Gram accumulator and workspace
+    const int32_t *idx;
+    const float *val;
+    int64_t n;
+    double *G;
+    void *work;
+};
+struct GramBatchInfo {
+    size_t tc_off, bk_off, slab_off, cta_off, smem;
+    int64_t slabs, ctas;
+    int nd, first;
+};
+cudaError_t gram_batch_build(const sk_ctx *ctxs, const BatchGram *rows, int nd, int mode,
+                             std::vector<unsigned char> &table, GramBatchInfo &info);
+cudaError_t gram_batch_launch(const GramBatchInfo &info, unsigned char *dev_table, cudaStream_t s);
+struct BatchKmeans {  // one data set's ELL rows and K-means state
+    const int32_t *idx;
+    const float *val;
+    int64_t n;
+    int K;
+    float *mu;
+    int32_t *labels;
+    double *S;
+    int32_t *cnt;
+    int64_t *nk;
+    int64_t *changed;
+};
+struct KmeansBatchInfo {
+    size_t params_off, tasks_off, start_off, ticket_off, smem;
+    int64_t total;
+    int nd, ntasks, grid, mu_cap;
+};
+cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd,
+                               std::vector<unsigned char> &table, KmeansBatchInfo &info);
+// op: 0 reset the sums, 1 full pass, 2 incremental pass, 3 finalize the centres
+cudaError_t kmeans_batch_launch(const KmeansBatchInfo &info, unsigned char *dev_table, int op,
+                                cudaStream_t s);
+
 cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
                             int64_t row0, int32_t *idx, float *val, float *Y,
                             cudaStream_t s);

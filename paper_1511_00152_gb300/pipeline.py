@@ -122,3 +122,93 @@ def pca(ctx: sk.Ctx, C, k: int, iters: int = 40):
     (U = (HD)^T U', Sec. V).  Returns (evals, U' [k x pt], U [k x p])."""
     evals, Up = sk.sk_cov_topk(ctx, C, k, iters)
     return evals, Up, sk.sk_unmix(ctx, Up)
+
+
+class BatchRun:
+    """Many independent data sets through the hot path with one launch per
+    stage (sk_batch_*): compress, Gram, and each K-means pass cover every data
+    set; the K-means loop is captured once as a CUDA graph.
+
+    datasets: list of dicts with X (device n x p float32), m, K, seed (and
+    optionally flags).  Buffers are allocated here with torch."""
+
+    def __init__(self, datasets, mode: int = sk.SK_GRAM_BF16, device="cuda"):
+        self.mode = mode
+        self.ds = []
+        items = []
+        for d in datasets:
+            X = d["X"]
+            n, p = X.shape
+            ctx = sk.sk_init_ex(p, d["m"], d["seed"], d.get("flags", 0))
+            pt, m, K = ctx.pt, ctx.m, d["K"]
+            e = dict(ctx=ctx, X=X, n=n, K=K, seed=d["seed"])
+            e["idx"] = torch.empty((n, m), dtype=torch.int32, device=device)
+            e["val"] = torch.empty((n, m), dtype=torch.float32, device=device)
+            e["G"] = torch.empty((pt, pt), dtype=torch.float64, device=device)
+            wb = sk.sk_cov_workspace_bytes(ctx, mode, n)
+            e["work"] = torch.empty(max(wb, 256), dtype=torch.uint8, device=device)
+            e["mu"] = torch.empty((K, pt), dtype=torch.float32, device=device)
+            e["labels"] = torch.empty(n, dtype=torch.int32, device=device)
+            e["S"] = torch.empty((K, pt), dtype=torch.float64, device=device)
+            e["cnt"] = torch.empty((K, pt), dtype=torch.int32, device=device)
+            e["nk"] = torch.empty(K, dtype=torch.int64, device=device)
+            e["changed"] = torch.zeros(1, dtype=torch.int64, device=device)
+            # the seeded start rows, selected once (input preparation)
+            rows = torch.as_tensor(synth_init_rows(n, K, d["seed"]), device=device)
+            e["Xsel"] = X.index_select(0, rows).contiguous()
+            self.ds.append(e)
+            items.append(sk.SkBatchItem(
+                p=p, m=m, seed=int(d["seed"]) & (2**64 - 1), flags=d.get("flags", 0),
+                X=X.data_ptr(), n=n, ldx=X.stride(0) if n > 1 else p, row0=0,
+                idx=e["idx"].data_ptr(), val=e["val"].data_ptr(), G=e["G"].data_ptr(),
+                gram_work=e["work"].data_ptr(), gram_work_bytes=e["work"].numel(), K=K,
+                mu=e["mu"].data_ptr(), labels=e["labels"].data_ptr(), S=e["S"].data_ptr(),
+                cnt=e["cnt"].data_ptr(), nk=e["nk"].data_ptr(), changed=e["changed"].data_ptr()))
+        self.batch = sk.sk_batch_create(items, mode, keep=self.ds)
+        self.table = torch.empty(max(256, sk.sk_batch_workspace_bytes(self.batch)),
+                                 dtype=torch.uint8, device=device)
+        sk.sk_batch_upload(self.batch, self.table)
+        self.graph = None
+        self._graph_iters = None
+
+    def compress_and_cov(self, stream=None):
+        """Compress every data set, then its Gram (one launch each stage)."""
+        sk.sk_batch_compress(self.batch, stream=stream)
+        sk.sk_batch_cov_reset(self.batch, stream=stream)
+        sk.sk_batch_cov_accumulate(self.batch, stream=stream)
+
+    def init_centres(self, stream=None):
+        """Seeded start: the preconditioned K seeded rows of each data set."""
+        for e in self.ds:
+            sk.sk_precondition(e["ctx"], e["Xsel"], Y=e["mu"], stream=stream)
+
+    def _loop(self, iters, stream=None):
+        sk.sk_batch_kmeans_reset(self.batch, stream=stream)
+        for it in range(iters):
+            sk.sk_batch_kmeans_step(self.batch, incremental=it > 0, stream=stream)
+            sk.sk_batch_kmeans_finalize(self.batch, stream=stream)
+
+    def kmeans(self, iters: int, use_graph: bool = True):
+        """iters passes over every data set from the current centres."""
+        if not use_graph:
+            self._loop(iters)
+            return
+        if self.graph is None or self._graph_iters != iters:
+            saved = [e["mu"].clone() for e in self.ds]
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                self._loop(min(iters, 2), stream=s)
+            torch.cuda.current_stream().wait_stream(s)
+            for e, m0 in zip(self.ds, saved):
+                e["mu"].copy_(m0)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._loop(iters)
+            self.graph, self._graph_iters = g, iters
+        self.graph.replay()
+
+
+def synth_init_rows(n, K, seed):
+    from . import synth
+    return synth.init_rows(n, K, seed)

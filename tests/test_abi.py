@@ -53,3 +53,16 @@ def test_host_validation_without_gpu():
     assert lib.sk_mean_finalize(h, nul, 0, nul, nul) == _lib.SK_EINVAL
     lib.sk_destroy(h)
     assert lib.sk_flags(nul) == 0
+    # batch plans validate their items on the host before any CUDA call
+    it = _lib.SkBatchItem(p=100, m=5, seed=1, n=10, ldx=100, K=3)
+    b = ctypes.c_void_p(0)
+    assert lib.sk_batch_create(ctypes.byref(b), ctypes.cast(ctypes.pointer(it), ctypes.c_void_p), 1,
+                               _lib.SK_GRAM_BF16) == _lib.SK_EUNSUPPORTED  # pt = 128
+    it = _lib.SkBatchItem(p=512, m=5, seed=1, n=10, ldx=512, K=100)
+    assert lib.sk_batch_create(ctypes.byref(b), ctypes.cast(ctypes.pointer(it), ctypes.c_void_p), 1,
+                               _lib.SK_GRAM_BF16) == _lib.SK_EUNSUPPORTED  # K > 64
+    it = _lib.SkBatchItem(p=512, m=5, seed=1, n=10, ldx=512, K=4)
+    assert lib.sk_batch_create(ctypes.byref(b), ctypes.cast(ctypes.pointer(it), ctypes.c_void_p), 1,
+                               _lib.SK_GRAM_BF16) == _lib.SK_EINVAL  # NULL buffers
+    assert b"NULL" in lib.sk_last_error()
+    assert lib.sk_batch_workspace_bytes(nul) == -1

@@ -1,0 +1,111 @@
+"""Many data sets, one launch per stage (sk_batch_*): every data set's
+result equals the single-data-set call on the same inputs.
+
+  idx, val         bit-exact (same kernel code per data set)
+  Gram G           1e-12 relative Frobenius (the same products; only the
+                   order of the float64 atomic adds differs)
+  labels           identical (same per-row arithmetic), teacher forced
+  cnt, nk          exact
+  S, centres       1e-6 relative (float partial sums in another order)
+"""
+import numpy as np
+import pytest
+
+from paper_1511_00152_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SETS = [  # (n, p, m, K, seed)
+    (3000, 256, 13, 5, 1),
+    (1777, 1000, 51, 10, 2),
+    (500, 2048, 102, 8, 3),
+    (2100, 4096, 82, 20, 4),
+    (64, 8192, 819, 50, 5),
+    (4097, 512, 26, 33, 6),
+]
+
+
+@pytest.fixture(scope="module")
+def run():
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import pipeline
+    ds = []
+    for (n, p, m, K, seed) in SETS:
+        X, _, _ = synth.mixture_device(n, p, min(K, 10), seed)
+        ds.append(dict(X=X, m=m, K=K, seed=seed))
+    br = pipeline.BatchRun(ds, mode=sk.SK_GRAM_BF16)
+    br.compress_and_cov()
+    br.init_centres()
+    torch.cuda.synchronize()
+    return sk, br
+
+
+def test_batch_compress_and_gram_match_single(run):
+    sk, br = run
+    for e in br.ds:
+        ctx = e["ctx"]
+        idx, val = sk.sk_compress(ctx, e["X"])
+        G = torch.zeros_like(e["G"])
+        sk.sk_cov_accumulate(ctx, sk.SK_GRAM_BF16, idx, val, G)
+        torch.cuda.synchronize()
+        assert torch.equal(idx, e["idx"])
+        assert torch.equal(val, e["val"])
+        U1, U2 = torch.triu(G), torch.triu(e["G"])
+        rel = (torch.linalg.norm(U1 - U2) / torch.linalg.norm(U1)).item()
+        assert rel <= 1e-12, rel
+    assert sk.sk_device_status() == sk.SK_OK
+
+
+def test_batch_kmeans_pass_matches_single(run):
+    sk, br = run
+    mus = [e["mu"].clone() for e in br.ds]
+    sk.sk_batch_kmeans_reset(br.batch)
+    sk.sk_batch_kmeans_step(br.batch, incremental=False)
+    torch.cuda.synchronize()
+    for e, mu in zip(br.ds, mus):
+        ctx, n, K = e["ctx"], e["n"], e["K"]
+        lab = torch.empty(n, dtype=torch.int32, device="cuda")
+        S = torch.zeros_like(e["S"])
+        cnt = torch.zeros_like(e["cnt"])
+        nk = torch.zeros_like(e["nk"])
+        sk.sk_kmeans_step(ctx, e["idx"], e["val"], mu, lab, S, cnt, nk)
+        torch.cuda.synchronize()
+        assert torch.equal(lab, e["labels"])
+        assert torch.equal(cnt, e["cnt"]) and torch.equal(nk, e["nk"])
+        sc = S.abs().max().item() + 1e-30
+        assert (S - e["S"]).abs().max().item() <= 1e-6 * sc
+    # finalize, then an incremental pass against the single-data-set delta
+    sk.sk_batch_kmeans_finalize(br.batch)
+    torch.cuda.synchronize()
+    ref = []
+    for e in br.ds:
+        st = dict(mu=e["mu"].clone(), labels=e["labels"].clone(), S=e["S"].clone(),
+                  cnt=e["cnt"].clone(), nk=e["nk"].clone())
+        sk.sk_kmeans_step_delta(e["ctx"], e["idx"], e["val"], st["mu"], st["labels"], st["S"],
+                                st["cnt"], st["nk"])
+        ref.append(st)
+    sk.sk_batch_kmeans_step(br.batch, incremental=True)
+    torch.cuda.synchronize()
+    for e, st in zip(br.ds, ref):
+        assert torch.equal(st["labels"], e["labels"])
+        assert torch.equal(st["cnt"], e["cnt"]) and torch.equal(st["nk"], e["nk"])
+    assert sk.sk_device_status() == sk.SK_OK
+
+
+def test_batch_graph_loop_matches_eager(run):
+    sk, br = run
+    br.init_centres()
+    br.kmeans(6, use_graph=False)
+    torch.cuda.synchronize()
+    eager = [(e["labels"].clone(), e["mu"].clone()) for e in br.ds]
+    br.init_centres()
+    br.kmeans(6, use_graph=True)
+    torch.cuda.synchronize()
+    for e, (l0, m0) in zip(br.ds, eager):
+        assert float((e["labels"] == l0).float().mean()) >= 0.999
+        assert torch.allclose(e["mu"], m0, rtol=1e-5, atol=1e-6)
+        nk = e["nk"].cpu().numpy()
+        assert nk.sum() == e["n"]
+        assert np.array_equal(e["cnt"].cpu().numpy().sum(axis=1), e["ctx"].m * nk)
+    assert sk.sk_device_status() == sk.SK_OK
