@@ -552,6 +552,117 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ batching
+
+BATCHING = dict(workload="batch64_mixtures_p256-8192_n1e4-5e5", datasets=64, iters=15,
+                seed=4242)
+
+
+def batching_sets(cfg):
+    """64 seeded data-set shapes: p from {256, ..., 8192}, n log-uniform in
+    [1e4, 5e5], m / p in {2%, 5%, 10%}, K in [5, 50]."""
+    import numpy as np
+    rng = np.random.default_rng(cfg["seed"])
+    out = []
+    for d in range(cfg["datasets"]):
+        p = int(2 ** rng.integers(8, 14))
+        n = int(np.exp(rng.uniform(np.log(1e4), np.log(5e5))))
+        gamma = float(rng.choice([0.02, 0.05, 0.10]))
+        m = max(2, int(round(gamma * p)))
+        K = int(rng.integers(5, 51))
+        out.append(dict(n=n, p=p, m=m, K=K, seed=cfg["seed"] * 1000 + d))
+    return out
+
+
+def run_batching(args):
+    """Config 4: 64 data sets through compress, BF16 Gram and 15 K-means
+    iterations, one launch per stage for all data sets (the K-means loop as a
+    CUDA graph), tiles picked by the library's autotuner.  Reports samples/s
+    over all rows and the step time against the sum of the per-data-set
+    roofline times of the three stages."""
+    import torch
+    from paper_1511_00152_gb300 import build as skbuild
+    skbuild.build()
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import pipeline, synth
+    cfg = dict(BATCHING)
+    shapes = batching_sets(cfg)
+    ds = []
+    for sh in shapes:
+        X, _, _ = synth.mixture_device(sh["n"], sh["p"], sh["K"], sh["seed"], heavy_frac=0.0)
+        ds.append(dict(X=X, m=sh["m"], K=sh["K"], seed=sh["seed"]))
+    torch.cuda.synchronize()
+    br = pipeline.BatchRun(ds, mode=sk.SK_GRAM_BF16)
+    tuning = br.autotune()
+    iters = cfg["iters"]
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        br.compress_and_cov()
+        if ev is not None:
+            ev[1].record(stream)
+        br.init_centres()
+        br.kmeans(iters, use_graph=True)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    a.record(stream)
+    for k in range(steps):
+        step(evs[k])
+    b.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = a.elapsed_time(b) / steps
+    t_cc = sum(e[0].elapsed_time(e[1]) for e in evs) / steps
+    t_km = sum(e[1].elapsed_time(e[2]) for e in evs) / steps
+    assert sk.sk_device_status() == sk.SK_OK
+    hbm, bf16, bf16s, src = load_peaks()
+    rows = sum(sh["n"] for sh in shapes)
+    # summed roofline times: compress and K-means passes on HBM bytes, the
+    # Gram on the tensor-core work it issues (128 x N tiles over all rows)
+    tn = tuning[1]
+    comp_b = sum(sh["n"] * (4 * sh["p"] + 8 * sh["m"]) for sh in shapes)
+    km_b = iters * sum(sh["n"] * (8 * sh["m"] + 8) for sh in shapes)
+    flops = 0.0
+    for sh in shapes:
+        pt = sh["p"]
+        N = tn if pt >= tn else pt
+        tiles = sum(pt // N - bi // (N // 128) for bi in range(pt // 128))
+        flops += 2.0 * sh["n"] * 128 * N * tiles
+    t_roof = (comp_b / (hbm * 1e9) + km_b / (hbm * 1e9) + flops / (bf16s * 1e12)) * 1e3
+    line = {
+        "metric": "samples/s of many data sets, one launch per stage (compress+BF16 Gram+"
+                  "15 K-means iters)",
+        "value": rows / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "datasets": len(shapes), "rows": rows,
+                   "kmeans_iters": iters, "gram": "bf16", "seed": cfg["seed"],
+                   "autotuned": {"compress_units_per_group": tuning[0],
+                                 "gram_tile_n": tuning[1]}},
+        "stage_ms": {"compress_and_gram": t_cc, "kmeans_start_and_loop": t_km},
+        "roofline": {"bound": "mixed (sum of per-data-set rooflines)",
+                     "time_ms": t_roof, "achieved_frac": t_roof / ms,
+                     "compress_bytes": comp_b, "kmeans_bytes": km_b, "gram_flops": flops,
+                     "peak_hbm_gbs": hbm, "peak_bf16_tflops": bf16s, "peak_source": src},
+        "clocks": clocks,
+        "gpu_launches_per_step": 1 + 2 + len(shapes) + 1 + 2 * iters,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,11 +678,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the K-means loop kernel by kernel (for profilers)")
-    ap.add_argument("--workload", default="kmeans", choices=["kmeans", "serving"],
-                    help="kmeans: the main step (default); serving: the streaming request loop")
+    ap.add_argument("--workload", default="kmeans", choices=["kmeans", "serving", "batching"],
+                    help="kmeans: the main step (default); serving: the streaming request loop; "
+                         "batching: 64 data sets, one launch per stage")
     args = ap.parse_args()
     if args.workload == "serving" and args.impl != "reference":
         return run_serving(args)
+    if args.workload == "batching" and args.impl != "reference":
+        return run_batching(args)
     cfg = dict(WORKLOAD)
     if args.n:
         cfg["n"] = args.n

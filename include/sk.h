@@ -355,8 +355,32 @@ sk_status sk_batch_kmeans_step(const sk_batch *b, int32_t incremental, void *str
 /* sk_kmeans_finalize of every data set in one launch. */
 sk_status sk_batch_kmeans_finalize(const sk_batch *b, void *stream);
 
+/* Autotuner of a batch (no paper counterpart): times the candidate compress
+ * task sizes (32 or 128 units per row group) and Gram tile widths (256 or
+ * 128 columns) on the batch's own data, keeps the fastest, rebuilds the plan
+ * and uploads it to `work` (sk_batch_workspace_bytes bytes covers every
+ * candidate).  Runs the compress and Gram stages (overwriting idx, val and
+ * G) and synchronises the stream: call it before capture, then reset G.
+ * The chosen sizes are written to the out-pointers when not NULL. */
+sk_status sk_batch_autotune(sk_batch *b, void *work, int64_t work_bytes, void *stream,
+                            int32_t *units_per_group, int32_t *gram_tile_n);
+
 /* Frees a plan (NULL is ignored). */
 void sk_batch_destroy(sk_batch *b);
+
+/* Autotuners of one handle (no paper counterpart): each times its candidate
+ * launch shapes on the caller's data with CUDA events, stores the fastest in
+ * the handle (used by later calls with it) and reports it.  They synchronise
+ * the stream and overwrite their outputs; call them before stream capture.
+ * sk_autotune_gram: tile width 256 or 128 columns times a row-split
+ * multiplier 1 or 2 for sk_cov_accumulate in `mode` (tensor-core modes,
+ * pt >= 256; G is overwritten -- reset it afterwards).
+ * sk_autotune_compress: 1 CTA per SM or as many as fit for sk_compress. */
+sk_status sk_autotune_gram(sk_ctx *ctx, int mode, const int32_t *idx, const float *val,
+                           int64_t n, double *G, void *work, int64_t work_bytes, void *stream,
+                           int32_t *tile_n, int32_t *split_mult);
+sk_status sk_autotune_compress(sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
+                               int32_t *idx, float *val, void *stream, int32_t *ctas_per_sm);
 
 /* Reports SK_ETIMEOUT if a bounded device wait of this library ran out since
  * the last call (and clears the flag), SK_ECUDA on a pending CUDA error, else

@@ -85,6 +85,10 @@ def load(path: str | None = None):
             "sk_batch_kmeans_step": (st, [vp, i32, vp]),
             "sk_batch_kmeans_finalize": (st, [vp, vp]),
             "sk_batch_destroy": (None, [vp]),
+            "sk_batch_autotune": (st, [vp, vp, i64, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "sk_autotune_gram": (st, [vp, ctypes.c_int, vp, vp, i64, vp, vp, i64, vp,
+                                      ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "sk_autotune_compress": (st, [vp, vp, i64, i64, vp, vp, vp, ctypes.POINTER(i32)]),
             "sk_device_status": (st, [vp]),
             "sk_last_error": (ctypes.c_char_p, []),
         }
@@ -471,6 +475,38 @@ def sk_batch_kmeans_step(b: Batch, incremental: bool, stream=None):
 
 def sk_batch_kmeans_finalize(b: Batch, stream=None):
     _check("sk_batch_kmeans_finalize", load().sk_batch_kmeans_finalize(b.handle, _stream(stream)))
+
+
+def sk_batch_autotune(b: Batch, work, stream=None):
+    """Returns (units per row group, Gram tile width) chosen by the library."""
+    u, t = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check("sk_batch_autotune", load().sk_batch_autotune(b.handle, _ptr(work),
+                                                         work.numel() * work.element_size(),
+                                                         _stream(stream), ctypes.byref(u),
+                                                         ctypes.byref(t)))
+    return int(u.value), int(t.value)
+
+
+def sk_autotune_gram(ctx: Ctx, mode: int, idx, val, G, work=None, stream=None):
+    """Returns (tile width, split multiplier); G is overwritten."""
+    n = idx.shape[0]
+    need = sk_cov_workspace_bytes(ctx, mode, n)
+    if work is None:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=idx.device)
+    a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check("sk_autotune_gram", load().sk_autotune_gram(
+        ctx.handle, int(mode), _ptr(idx), _ptr(val), n, _ptr(G), _ptr(work),
+        work.numel() * work.element_size(), _stream(stream), ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
+
+
+def sk_autotune_compress(ctx: Ctx, X, idx, val, stream=None):
+    """Returns the chosen CTAs per SM (0: as many as fit); idx/val are overwritten."""
+    n, ldx = _rows_ld(X, ctx.p)
+    c = ctypes.c_int32(0)
+    _check("sk_autotune_compress", load().sk_autotune_compress(
+        ctx.handle, _ptr(X), n, ldx, _ptr(idx), _ptr(val), _stream(stream), ctypes.byref(c)))
+    return int(c.value)
 
 
 def sk_batch_destroy(b: Batch):

@@ -14,12 +14,67 @@ struct sk_batch {
     std::vector<sk_batch_item> items;
     int nd = 0;
     int mode = 0;
+    int units_per_group = 64;  // compress task size (units per row group)
+    int gram_n = 256;          // Gram tile width of the multi-data-set launch
+    size_t max_table = 0;      // largest table over the autotuner's candidates
     std::vector<unsigned char> table;
     sk::CompressBatchInfo ci{};
     sk::GramBatchInfo gi{};
     sk::KmeansBatchInfo ki{};
     unsigned char *dev = nullptr;
 };
+
+// (Re)builds the device tables of a plan for the given launch shapes.
+static cudaError_t build_tables(sk_batch *B, int units_per_group, int gram_n) {
+    const int nd = B->nd;
+    std::vector<sk::BatchRows> rows((size_t)nd);
+    std::vector<sk::BatchGram> grams((size_t)nd);
+    std::vector<sk::BatchKmeans> kms((size_t)nd);
+    for (int d = 0; d < nd; ++d) {
+        const sk_batch_item &it = B->items[d];
+        rows[d] = sk::BatchRows{it.X, it.n, it.ldx, it.row0, it.idx, it.val};
+        grams[d] = sk::BatchGram{it.idx, it.val, it.n, it.G, it.gram_work};
+        kms[d] = sk::BatchKmeans{it.idx, it.val, it.n, it.K, it.mu, it.labels,
+                                 it.S,   it.cnt, it.nk, it.changed};
+        B->ctxs[d].gram_n = gram_n;
+    }
+    B->table.clear();
+    cudaError_t e = sk::compress_batch_build(B->ctxs.data(), rows.data(), nd, units_per_group,
+                                             B->table, B->ci);
+    if (e == cudaSuccess)
+        e = sk::gram_batch_build(B->ctxs.data(), grams.data(), nd, B->mode, B->table, B->gi);
+    if (e == cudaSuccess) e = sk::kmeans_batch_build(B->ctxs.data(), kms.data(), nd, B->table, B->ki);
+    if (e == cudaSuccess) {
+        B->units_per_group = units_per_group;
+        B->gram_n = gram_n;
+    }
+    return e;
+}
+
+// Milliseconds of one call of fn (after one untimed call), on the stream.
+template <typename F>
+static cudaError_t time_ms(F fn, cudaStream_t s, float &ms) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
+static const int kUnitsCand[] = {32, 128};
+static const int kGramNCand[] = {256, 128};
 
 namespace {
 
@@ -103,20 +158,15 @@ sk_status sk_batch_create(sk_batch **b, const sk_batch_item *items, int32_t nd,
     B->items.assign(items, items + nd);
     B->nd = nd;
     B->mode = gram_mode;
-    std::vector<sk::BatchRows> rows((size_t)nd);
-    std::vector<sk::BatchGram> grams((size_t)nd);
-    std::vector<sk::BatchKmeans> kms((size_t)nd);
-    for (int d = 0; d < nd; ++d) {
-        const sk_batch_item &it = items[d];
-        rows[d] = sk::BatchRows{it.X, it.n, it.ldx, it.row0, it.idx, it.val};
-        grams[d] = sk::BatchGram{it.idx, it.val, it.n, it.G, it.gram_work};
-        kms[d] = sk::BatchKmeans{it.idx, it.val, it.n, it.K, it.mu, it.labels,
-                                 it.S,   it.cnt, it.nk, it.changed};
-    }
-    cudaError_t e = sk::compress_batch_build(B->ctxs.data(), rows.data(), nd, 64, B->table, B->ci);
-    if (e == cudaSuccess)
-        e = sk::gram_batch_build(B->ctxs.data(), grams.data(), nd, gram_mode, B->table, B->gi);
-    if (e == cudaSuccess) e = sk::kmeans_batch_build(B->ctxs.data(), kms.data(), nd, B->table, B->ki);
+    // the autotuner's candidates may need a larger table than the default
+    cudaError_t e = cudaSuccess;
+    for (int u : kUnitsCand)
+        for (int gn : kGramNCand) {
+            if (e == cudaSuccess) e = build_tables(B, u, gn);
+            if (e == cudaSuccess && B->table.size() > B->max_table) B->max_table = B->table.size();
+        }
+    if (e == cudaSuccess) e = build_tables(B, 64, 256);
+    if (e == cudaSuccess && B->table.size() > B->max_table) B->max_table = B->table.size();
     if (e != cudaSuccess) {
         delete B;
         if (e == cudaErrorInvalidValue)
@@ -128,7 +178,7 @@ sk_status sk_batch_create(sk_batch **b, const sk_batch_item *items, int32_t nd,
 }
 
 int64_t sk_batch_workspace_bytes(const sk_batch *b) {
-    return b ? (int64_t)b->table.size() : -1;
+    return b ? (int64_t)b->max_table : -1;
 }
 
 sk_status sk_batch_upload(sk_batch *b, void *work, int64_t work_bytes, void *stream) {
@@ -195,6 +245,48 @@ sk_status sk_batch_kmeans_finalize(const sk_batch *b, void *stream) {
     if (st != SK_OK) return st;
     return bcuda(sk::kmeans_batch_launch(b->ki, b->dev, 3, bstream(stream)),
                  "sk_batch_kmeans_finalize");
+}
+
+sk_status sk_batch_autotune(sk_batch *b, void *work, int64_t work_bytes, void *stream,
+                            int32_t *units_per_group, int32_t *gram_tile_n) {
+    if (!b || !work) return bfail(SK_EINVAL, "sk_batch_autotune: NULL argument");
+    if (work_bytes < (int64_t)b->max_table)
+        return bfail(SK_EINVAL, "sk_batch_autotune: %lld bytes needed", (long long)b->max_table);
+    cudaStream_t s = bstream(stream);
+    float best = 1e30f;
+    int best_u = b->units_per_group, best_n = b->gram_n;
+    for (int u : kUnitsCand) {
+        cudaError_t e = build_tables(b, u, best_n);
+        sk_status st = e == cudaSuccess ? sk_batch_upload(b, work, work_bytes, stream) : bcuda(e, "sk_batch_autotune");
+        if (st != SK_OK) return st;
+        float ms = 0.f;
+        e = time_ms([&] { return sk::compress_batch_launch(b->ci, b->dev, s); }, s, ms);
+        if (e != cudaSuccess) return bcuda(e, "sk_batch_autotune (compress)");
+        if (ms < best) {
+            best = ms;
+            best_u = u;
+        }
+    }
+    best = 1e30f;
+    for (int gn : kGramNCand) {
+        cudaError_t e = build_tables(b, best_u, gn);
+        sk_status st = e == cudaSuccess ? sk_batch_upload(b, work, work_bytes, stream) : bcuda(e, "sk_batch_autotune");
+        if (st != SK_OK) return st;
+        float ms = 0.f;
+        e = time_ms([&] { return sk::gram_batch_launch(b->gi, b->dev, s); }, s, ms);
+        if (e != cudaSuccess) return bcuda(e, "sk_batch_autotune (Gram)");
+        if (ms < best) {
+            best = ms;
+            best_n = gn;
+        }
+    }
+    cudaError_t e = build_tables(b, best_u, best_n);
+    if (e != cudaSuccess) return bcuda(e, "sk_batch_autotune");
+    sk_status st = sk_batch_upload(b, work, work_bytes, stream);
+    if (st != SK_OK) return st;
+    if (units_per_group) *units_per_group = best_u;
+    if (gram_tile_n) *gram_tile_n = best_n;
+    return SK_OK;
 }
 
 void sk_batch_destroy(sk_batch *b) { delete b; }

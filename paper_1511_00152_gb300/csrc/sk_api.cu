@@ -369,6 +369,114 @@ sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_tota
                        "sk_mean_finalize");
 }
 
+static cudaError_t time_call_ms(cudaStream_t s, float &ms, cudaError_t (*fn)(void *), void *arg) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    e = fn(arg);  // untimed first call (launch attributes, caches)
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = fn(arg);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
+namespace {
+struct GramCall {
+    sk_ctx *c;
+    int mode;
+    const int32_t *idx;
+    const float *val;
+    int64_t n;
+    double *G;
+    void *work;
+    cudaStream_t s;
+};
+cudaError_t gram_call(void *p) {
+    GramCall *g = static_cast<GramCall *>(p);
+    return sk::launch_gram_tc(*g->c, g->mode, g->idx, g->val, g->n, g->G, g->work, g->s);
+}
+struct CompressCall {
+    sk_ctx *c;
+    const float *X;
+    int64_t n, ldx;
+    int32_t *idx;
+    float *val;
+    cudaStream_t s;
+};
+cudaError_t compress_call(void *p) {
+    CompressCall *q = static_cast<CompressCall *>(p);
+    return sk::launch_compress(*q->c, q->X, q->n, q->ldx, 0, q->idx, q->val, nullptr, q->s);
+}
+}  // namespace
+
+sk_status sk_autotune_gram(sk_ctx *ctx, int mode, const int32_t *idx, const float *val, int64_t n,
+                           double *G, void *work, int64_t work_bytes, void *stream,
+                           int32_t *tile_n, int32_t *split_mult) {
+    SK_CHECK_CTX(ctx);
+    if (mode != SK_GRAM_BF16 && mode != SK_GRAM_BF16X3)
+        return fail(SK_EINVAL, "sk_autotune_gram: tensor-core modes only");
+    if (ctx->pt < 256) return fail(SK_EUNSUPPORTED, "sk_autotune_gram: needs pt >= 256");
+    if (n < 1 || !idx || !val || !G || !work) return fail(SK_EINVAL, "sk_autotune_gram: bad argument");
+    if (work_bytes < sk::gram_tc_workspace(*ctx, n))
+        return fail(SK_EINVAL, "sk_autotune_gram: workspace too small");
+    GramCall g{ctx, mode, idx, val, n, G, work, as_stream(stream)};
+    const int cand_n[2] = {256, 128}, cand_s[2] = {1, 2};
+    float best = 1e30f;
+    int bn = 256, bs = 1;
+    for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) {
+            ctx->gram_n = cand_n[a];
+            ctx->split_mult = cand_s[c];
+            float ms = 0.f;
+            cudaError_t e = time_call_ms(g.s, ms, gram_call, &g);
+            if (e != cudaSuccess) return cuda_status(e, "sk_autotune_gram");
+            if (ms < best) {
+                best = ms;
+                bn = cand_n[a];
+                bs = cand_s[c];
+            }
+        }
+    ctx->gram_n = bn;
+    ctx->split_mult = bs;
+    if (tile_n) *tile_n = bn;
+    if (split_mult) *split_mult = bs;
+    g_msg[0] = 0;
+    return SK_OK;
+}
+
+sk_status sk_autotune_compress(sk_ctx *ctx, const float *X, int64_t n, int64_t ldx, int32_t *idx,
+                               float *val, void *stream, int32_t *ctas_per_sm) {
+    SK_CHECK_CTX(ctx);
+    if (n < 1 || ldx < ctx->p || !X || !idx || !val)
+        return fail(SK_EINVAL, "sk_autotune_compress: bad argument");
+    CompressCall q{ctx, X, n, ldx, idx, val, as_stream(stream)};
+    float best = 1e30f;
+    int bc = 0;
+    for (int c : {0, 1}) {
+        ctx->compress_ctas = c;
+        float ms = 0.f;
+        cudaError_t e = time_call_ms(q.s, ms, compress_call, &q);
+        if (e != cudaSuccess) return cuda_status(e, "sk_autotune_compress");
+        if (ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    ctx->compress_ctas = bc;
+    if (ctas_per_sm) *ctas_per_sm = bc;
+    g_msg[0] = 0;
+    return SK_OK;
+}
+
 sk_status sk_device_status(void *stream) {
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess) return cuda_status(e, "sk_device_status");

@@ -171,6 +171,13 @@ class BatchRun:
         self.graph = None
         self._graph_iters = None
 
+    def autotune(self):
+        """Library autotuner: compress task size and Gram tile width for this
+        batch (runs both stages once; call before capture)."""
+        self.tuning = sk.sk_batch_autotune(self.batch, self.table)
+        self.graph = None  # the plan's tables moved: recapture
+        return self.tuning
+
     def compress_and_cov(self, stream=None):
         """Compress every data set, then its Gram (one launch each stage)."""
         sk.sk_batch_compress(self.batch, stream=stream)

@@ -109,3 +109,47 @@ def test_batch_graph_loop_matches_eager(run):
         assert nk.sum() == e["n"]
         assert np.array_equal(e["cnt"].cpu().numpy().sum(axis=1), e["ctx"].m * nk)
     assert sk.sk_device_status() == sk.SK_OK
+
+
+def test_batch_autotune_keeps_results(run):
+    sk, br = run
+    br.compress_and_cov()
+    torch.cuda.synchronize()
+    idx0 = [e["idx"].clone() for e in br.ds]
+    G0 = [e["G"].clone() for e in br.ds]
+    u, t = br.autotune()
+    assert u in (32, 128) and t in (256, 128)
+    br.compress_and_cov()
+    torch.cuda.synchronize()
+    for e, i0, g0 in zip(br.ds, idx0, G0):
+        assert torch.equal(e["idx"], i0)
+        U0, U1 = torch.triu(g0), torch.triu(e["G"])
+        assert (torch.linalg.norm(U1 - U0) / torch.linalg.norm(U0)).item() <= 1e-5
+    br.init_centres()
+    br.kmeans(3, use_graph=True)
+    torch.cuda.synchronize()
+    for e in br.ds:
+        assert e["nk"].sum().item() == e["n"]
+    assert sk.sk_device_status() == sk.SK_OK
+
+
+def test_single_handle_autotuners():
+    from paper_1511_00152_gb300 import _lib as sk
+    n, p, m, seed = 20000, 1024, 51, 9
+    X, _, _ = synth.mixture_device(n, p, 10, seed)
+    ctx = sk.sk_init(p, m, seed)
+    idx, val = sk.sk_compress(ctx, X)
+    G0 = torch.zeros((ctx.pt, ctx.pt), dtype=torch.float64, device="cuda")
+    sk.sk_cov_accumulate(ctx, sk.SK_GRAM_BF16X3, idx, val, G0)
+    c = sk.sk_autotune_compress(ctx, X, torch.empty_like(idx), torch.empty_like(val))
+    assert c in (0, 1)
+    tn, sm = sk.sk_autotune_gram(ctx, sk.SK_GRAM_BF16X3, idx, val, torch.empty_like(G0))
+    assert tn in (128, 256) and sm in (1, 2)
+    idx2, val2 = sk.sk_compress(ctx, X)
+    G = torch.zeros_like(G0)
+    sk.sk_cov_accumulate(ctx, sk.SK_GRAM_BF16X3, idx2, val2, G)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, idx2) and torch.equal(val, val2)
+    U0, U1 = torch.triu(G0), torch.triu(G)
+    assert (torch.linalg.norm(U1 - U0) / torch.linalg.norm(U0)).item() <= 1e-6
+    assert sk.sk_device_status() == sk.SK_OK
