@@ -29,6 +29,13 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
   compress_raw    -- val = x[idx] with the (pinned) mask; raw padding is zero
   kmeans_2pass    -- brute-force dense distances and per-label means on small
                      inputs; converged Lloyd's is a fixed point (Algorithm 2)
+  kpp_draw        -- chi-square uniformity over [0, W); draws stay below W with
+                     a rejection rate near 1/2 (W = 2^63 + 1)
+  kmeanspp        -- first centre uniform over the rows (chi-square over
+                     restarts); second centre distributed as D^2 / sum D^2
+                     (chi-square per first centre, SODA'07 D^2 sampling);
+                     zero-distance duplicates never chosen; K = n distinct
+                     rows gives a permutation; centres are the rows' scatters
 """
 from __future__ import annotations
 
@@ -89,6 +96,8 @@ def _load():
             "oracle_unmix": (None, [vp, i64, i64, i64, u64, vp]),
             "oracle_compress_raw": (None, [vp, i64, i64, i64, i64, i64, u64, vp, vp]),
             "oracle_kmeans_2pass": (None, [vp, i64, i64, vp, vp, i64, vp, vp, vp]),
+            "oracle_kpp_draw": (u64, [u64, u32, u32, u64]),
+            "oracle_kmeanspp": (None, [vp, vp, i64, i64, i64, i64, u64, u32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -302,6 +311,23 @@ def kmeans_2pass(X, labels1, mu1):
     counts = np.zeros(K, np.int64)
     _load().oracle_kmeans_2pass(_p(X), n, p, _p(c1), _p(mu1), K, _p(c2), _p(mu2), _p(counts))
     return c2, mu2, counts
+
+
+def kpp_draw(seed: int, k: int, r: int, W: int) -> int:
+    """K-means++ draw of step k, restart r, uniform over [0, W)."""
+    return int(_load().oracle_kpp_draw(int(seed) & (2**64 - 1), k, r, W))
+
+
+def kmeanspp(idx, val, pt: int, K: int, seed: int, r: int = 0):
+    """K-means++ seeding on the ELL rows (val float32): (rows, centres K x pt float32)."""
+    idx = _c(idx, np.int32)
+    val = _c(val, np.float32)
+    n, m = idx.shape
+    rows = np.zeros(K, np.int64)
+    cen = np.zeros((K, pt), np.float32)
+    _load().oracle_kmeanspp(_p(idx), _p(val), n, m, pt, K, int(seed) & (2**64 - 1), r,
+                            _p(rows), _p(cen))
+    return rows, cen
 
 
 def unmix(M, p: int, seed: int) -> np.ndarray:

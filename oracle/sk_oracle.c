@@ -29,6 +29,23 @@
  *     emit a[t].  Indices are kept in draw order.
  *   Initial K-means rows (test harness): partial Fisher-Yates over [0,n)
  *     with words of Philox(ctr = (w/4, 0, 0, TAG_INIT)).
+ *   K-means++ seeding on the sparsified rows, restart r (Algorithm 1, "find
+ *     initial cluster centers via K-means++"; D. Arthur, S. Vassilvitskii,
+ *     "k-means++: the advantages of careful seeding", SODA 2007):
+ *     the draw of step k over [0, W) takes attempt a's 64-bit word
+ *     x = w[2(a%2)+1] 2^32 + w[2(a%2)] of Philox(ctr = (k, r, a/2,
+ *     TAG_KMPP)) and Lemire's multiply-shift on 64 bits (reject while the
+ *     low 64 bits of x W are below (2^64 - W) mod W; value = high 64 bits).
+ *     Step 0: the first centre is the draw over W = n.  Step k >= 1: D2_i is
+ *     the smallest restricted squared distance of row i to a chosen centre,
+ *     sum over t of (val_i[t] - w_c[idx_i[t]])^2 with w_c the pt-vector of
+ *     row c's ELL entries (zero elsewhere), formed in float32 (t ascending,
+ *     d = fmaf(v - c, v - c, d)); the weights are the integers
+ *     q_i = floor(D2_i 2^(B - e)), e the binary exponent of max_i D2_i
+ *     (max = f 2^e, 0.5 <= f < 1) and B = 62 - ceil(log2(n + 1)); the centre
+ *     is the first i whose inclusive prefix sum of q exceeds the draw over
+ *     W = sum q (if W = 0, the draw over n).  The integer weights make the
+ *     choice independent of summation order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -38,6 +55,7 @@
 #define TAG_SIGN 0x5349474Eu /* "SIGN" */
 #define TAG_MASK 0x4D41534Bu /* "MASK" */
 #define TAG_INIT 0x494E4954u /* "INIT" */
+#define TAG_KMPP 0x4B4D5050u /* "KMPP" */
 
 /* ---------------- Philox4x32-10 (Salmon et al., SC'11) ---------------- */
 
@@ -352,4 +370,81 @@ void oracle_kmeans_2pass(const float *X, int64_t n, int64_t p, const int32_t *c1
         for (int64_t j = 0; j < p; ++j)
             mu2[k * p + j] = counts[k] > 0 ? sum[k * p + j] / (double)counts[k] : mu1[k * p + j];
     free(sum);
+}
+
+/* ---------------- K-means++ seeding on sparse rows ---------------- */
+
+/* Draw of step k, restart r, uniform over [0, W) (W >= 1): 64-bit Lemire
+ * multiply-shift with rejection on the KMPP stream (header spec). */
+uint64_t oracle_kpp_draw(uint64_t seed, uint32_t k, uint32_t r, uint64_t W) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint64_t threshold = (0 - W) % W; /* (2^64 - W) mod W */
+    for (uint32_t a = 0;; ++a) {
+        const uint32_t ctr[4] = {k, r, a / 2, TAG_KMPP};
+        uint32_t out[4];
+        oracle_philox4x32_10(ctr, key, out);
+        const uint64_t x = ((uint64_t)out[2 * (a % 2) + 1] << 32) | out[2 * (a % 2)];
+        const __uint128_t prod = (__uint128_t)x * W;
+        if ((uint64_t)prod < threshold) continue;
+        return (uint64_t)(prod >> 64);
+    }
+}
+
+/* Restricted squared distance of ELL row i to the dense pt-vector cen, in
+ * float32 with t ascending (the precision the seeding decides in). */
+static float kpp_dist(const int32_t *idx, const float *val, int64_t i, int64_t m,
+                      const float *cen) {
+    float d = 0.0f;
+    for (int64_t t = 0; t < m; ++t) {
+        const float diff = val[i * m + t] - cen[idx[i * m + t]];
+        d = fmaf(diff, diff, d);
+    }
+    return d;
+}
+
+/* K-means++ seeding of restart r (header spec).  idx, val: the n x m ELL
+ * rows (val in float32).  rows_out: K chosen row indices; centres_out:
+ * K x pt, row k the dense pt-vector of the chosen row's entries. */
+void oracle_kmeanspp(const int32_t *idx, const float *val, int64_t n, int64_t m, int64_t pt,
+                     int64_t K, uint64_t seed, uint32_t r, int64_t *rows_out,
+                     float *centres_out) {
+    float *D2 = (float *)malloc((size_t)n * sizeof(float));
+    int B = 62;
+    while (((uint64_t)1 << (62 - B)) < (uint64_t)(n + 1)) --B; /* B = 62 - ceil(log2(n+1)) */
+    for (int64_t k = 0; k < K; ++k) {
+        int64_t c;
+        if (k == 0) {
+            c = (int64_t)oracle_kpp_draw(seed, 0u, r, (uint64_t)n);
+        } else {
+            float mx = 0.0f;
+            for (int64_t i = 0; i < n; ++i)
+                if (D2[i] > mx) mx = D2[i];
+            uint64_t W = 0;
+            int e = 0;
+            if (mx > 0.0f) {
+                frexp((double)mx, &e);
+                for (int64_t i = 0; i < n; ++i) W += (uint64_t)ldexp((double)D2[i], B - e);
+            }
+            if (W == 0) {
+                c = (int64_t)oracle_kpp_draw(seed, (uint32_t)k, r, (uint64_t)n);
+            } else {
+                const uint64_t u = oracle_kpp_draw(seed, (uint32_t)k, r, W);
+                uint64_t acc = 0;
+                c = n - 1;
+                for (int64_t i = 0; i < n; ++i) {
+                    acc += (uint64_t)ldexp((double)D2[i], B - e);
+                    if (acc > u) { c = i; break; }
+                }
+            }
+        }
+        rows_out[k] = c;
+        float *cen = centres_out + k * pt;
+        for (int64_t j = 0; j < pt; ++j) cen[j] = 0.0f;
+        for (int64_t t = 0; t < m; ++t) cen[idx[c * m + t]] = val[c * m + t];
+        for (int64_t i = 0; i < n; ++i) {
+            const float d = kpp_dist(idx, val, i, m, cen);
+            if (k == 0 || d < D2[i]) D2[i] = d;
+        }
+    }
+    free(D2);
 }
