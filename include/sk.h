@@ -238,6 +238,37 @@ sk_status sk_unmix(const sk_ctx *ctx, const float *in, int64_t r, float *out,
 sk_status sk_unmix_f64(const sk_ctx *ctx, const double *in, int64_t r, double *out,
                        void *stream);
 
+/* K-means++ seeding on the sparsified rows (Algorithm 1, "find initial
+ * cluster centers via K-means++"; Arthur & Vassilvitskii, SODA 2007), restart
+ * `restart` of the handle's seed.  Centre k is a row of the data: the
+ * pt-vector of the chosen row's ELL entries (zero elsewhere).  The first row
+ * is uniform; each next row is drawn with probability proportional to D2_i,
+ * the row's restricted squared distance to its nearest chosen centre.
+ * Bit-exact spec: D2_i = min over chosen c of sum_t (val_i[t] - w_c[idx_i[t]])^2
+ * in float32 (t ascending, d = fma(v - c, v - c, d)); integer weights
+ * q_i = floor(D2_i 2^(B - e)) with e the binary exponent of max D2
+ * (max = f 2^e, 0.5 <= f < 1) and B = 62 - ceil(log2(n + 1)); the centre is
+ * the first row whose inclusive prefix sum of q exceeds the draw over
+ * W = sum q (W = 0: a draw over n).  The draw of step k over [0, W) takes
+ * attempt a's word w[2(a%2)+1] 2^32 + w[2(a%2)] of Philox(ctr = (k, restart,
+ * a/2, 0x4B4D5050 "KMPP")) and Lemire's 64-bit multiply-shift, rejecting
+ * while the low 64 bits of x W are below (2^64 - W) mod W.
+ * idx, val: device n x m ELL rows; mu: device K x pt float32 (the centres,
+ * output); rows: device int64 K (the chosen rows, output); work: device
+ * scratch of sk_kmeanspp_workspace_bytes(ctx, n) bytes, 256-byte aligned.
+ * 1 <= K <= min(n, 256). */
+sk_status sk_kmeanspp(const sk_ctx *ctx, const int32_t *idx, const float *val, int64_t n,
+                      int32_t K, uint32_t restart, float *mu, int64_t *rows, void *work,
+                      int64_t work_bytes, void *stream);
+int64_t sk_kmeanspp_workspace_bytes(const sk_ctx *ctx, int64_t n);
+
+/* The objective J' of a run (Sec. VI-A): *J = sum of the n winning
+ * restricted distances `dist` (device float32, as written by the assignment
+ * calls), summed in float64 into the device scalar J (overwritten).  Used to
+ * keep the best of several restarts (Sec. VII: the run with the smallest
+ * objective). */
+sk_status sk_kmeans_objective(const float *dist, int64_t n, double *J, void *stream);
+
 /* Second pass of the 2-pass sparsified K-means (Algorithm 2), first half:
  * for each raw row x_i (X: device n x p float32, leading dimension ldx >= p),
  * labels[i] = argmin_k ||x_i - mu[k]||^2 over all p coordinates, ties to the

@@ -74,6 +74,9 @@ def load(path: str | None = None):
             "sk_kmeans2_sums": (st, [vp, vp, i64, i64, vp, i32, vp, vp, vp]),
             "sk_kmeans2_finalize": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_mean_accumulate": (st, [vp, vp, vp, i64, vp, vp]),
+            "sk_kmeanspp": (st, [vp, vp, vp, i64, i32, ctypes.c_uint32, vp, vp, vp, i64, vp]),
+            "sk_kmeanspp_workspace_bytes": (i64, [vp, i64]),
+            "sk_kmeans_objective": (st, [vp, i64, vp, vp]),
             "sk_mean_finalize": (st, [vp, vp, i64, vp, vp]),
             "sk_batch_create": (st, [ctypes.POINTER(vp), vp, i32, i32]),
             "sk_batch_workspace_bytes": (i64, [vp]),
@@ -380,6 +383,42 @@ def sk_kmeans2_finalize(ctx: Ctx, sums, counts, mu, stream=None):
                                                              _ptr(counts), _ptr(mu),
                                                              _stream(stream)))
     return mu
+
+
+def sk_kmeanspp_workspace_bytes(ctx: Ctx, n: int) -> int:
+    return int(load().sk_kmeanspp_workspace_bytes(ctx.handle, int(n)))
+
+
+def sk_kmeanspp(ctx: Ctx, idx, val, K: int, restart: int = 0, mu=None, rows=None, work=None,
+                stream=None):
+    """K-means++ seeding: (centres K x pt float32, chosen rows K int64), on the device."""
+    n = idx.shape[0]
+    _need(idx, torch.int32, "idx", (n, ctx.m))
+    _need(val, torch.float32, "val", (n, ctx.m))
+    dev = idx.device
+    if mu is None:
+        mu = torch.empty((K, ctx.pt), dtype=torch.float32, device=dev)
+    if rows is None:
+        rows = torch.empty(K, dtype=torch.int64, device=dev)
+    _need(mu, torch.float32, "mu", (K, ctx.pt))
+    _need(rows, torch.int64, "rows", (K,))
+    need = sk_kmeanspp_workspace_bytes(ctx, n)
+    if work is None:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    _check("sk_kmeanspp", load().sk_kmeanspp(ctx.handle, _ptr(idx), _ptr(val), n, int(K),
+                                             int(restart), _ptr(mu), _ptr(rows), _ptr(work),
+                                             work.numel() * work.element_size(), _stream(stream)))
+    return mu, rows
+
+
+def sk_kmeans_objective(dist, J=None, stream=None):
+    """J' = sum of the winning distances (device float64 scalar)."""
+    _need(dist, torch.float32, "dist")
+    if J is None:
+        J = torch.empty(1, dtype=torch.float64, device=dist.device)
+    _check("sk_kmeans_objective", load().sk_kmeans_objective(_ptr(dist), dist.numel(), _ptr(J),
+                                                             _stream(stream)))
+    return J
 
 
 def sk_mean_accumulate(ctx: Ctx, idx, val, sums, stream=None):

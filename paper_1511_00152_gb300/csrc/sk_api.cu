@@ -312,6 +312,35 @@ sk_status sk_unmix_f64(const sk_ctx *ctx, const double *in, int64_t r, double *o
                        "sk_unmix_f64");
 }
 
+int64_t sk_kmeanspp_workspace_bytes(const sk_ctx *ctx, int64_t n) {
+    if (!ctx || n < 0) return -1;
+    return sk::kmeanspp_workspace(n);
+}
+
+sk_status sk_kmeanspp(const sk_ctx *ctx, const int32_t *idx, const float *val, int64_t n,
+                      int32_t K, uint32_t restart, float *mu, int64_t *rows, void *work,
+                      int64_t work_bytes, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (n < 1) return fail(SK_EINVAL, "sk_kmeanspp: n < 1");
+    if (K < 1 || K > 256 || K > n) return fail(SK_EINVAL, "sk_kmeanspp: K = %d must be in [1, min(n, 256)]", K);
+    if (n > ((int64_t)1 << 40)) return fail(SK_EUNSUPPORTED, "sk_kmeanspp: n too large");
+    if (!idx || !val || !mu || !rows || !work) return fail(SK_EINVAL, "sk_kmeanspp: NULL buffer");
+    if (work_bytes < sk::kmeanspp_workspace(n))
+        return fail(SK_EINVAL, "sk_kmeanspp: workspace of %lld bytes needed",
+                    (long long)sk::kmeanspp_workspace(n));
+    if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
+        return fail(SK_EINVAL, "sk_kmeanspp: workspace must be 256-byte aligned");
+    return cuda_status(sk::launch_kmeanspp(*ctx, idx, val, n, K, restart, mu, rows, work,
+                                           as_stream(stream)),
+                       "sk_kmeanspp");
+}
+
+sk_status sk_kmeans_objective(const float *dist, int64_t n, double *J, void *stream) {
+    if (n < 0) return fail(SK_EINVAL, "sk_kmeans_objective: n < 0");
+    if (!J || (n > 0 && !dist)) return fail(SK_EINVAL, "sk_kmeans_objective: NULL buffer");
+    return cuda_status(sk::launch_objective(dist, n, J, as_stream(stream)), "sk_kmeans_objective");
+}
+
 sk_status sk_kmeans2_assign(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
                             const float *mu, int32_t K, int32_t *labels, float *dist,
                             void *stream) {

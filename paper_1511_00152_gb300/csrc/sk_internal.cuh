@@ -194,6 +194,12 @@ cudaError_t launch_cov_finalize(const sk_ctx &c, const double *G, int64_t n_tota
                                 double *C, cudaStream_t s);
 cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out,
                          bool f64, cudaStream_t s);
+// K-means++ seeding and the objective J' (kmeanspp.cu).
+int64_t kmeanspp_workspace(int64_t n);
+cudaError_t launch_kmeanspp(const sk_ctx &c, const int32_t *idx, const float *val, int64_t n,
+                            int K, uint32_t restart, float *mu, int64_t *rows, void *work,
+                            cudaStream_t s);
+cudaError_t launch_objective(const float *dist, int64_t n, double *J, cudaStream_t s);
 // Algorithm 2's second pass and the sample mean (extras.cu).
 cudaError_t launch_kmeans2_assign(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
                                   const float *mu, int K, int32_t *labels, float *dist,

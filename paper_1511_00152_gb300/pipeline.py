@@ -73,6 +73,32 @@ class KMeansState:
         return self.labels, self.mu
 
 
+def kmeans_best_of(ctx: sk.Ctx, idx, val, K: int, restarts: int, iters: int,
+                   use_graph: bool = True):
+    """Sparsified K-means from K-means++ starts, best of `restarts` runs by the
+    objective J' (Algorithm 1 with K-means++ seeding; Sec. VII keeps the run
+    with the smallest objective).  The seeding, the iterations and J' run in
+    the library; the host only compares the R objective values.
+    Returns (labels, centres mu' [K x pt], J', best restart)."""
+    n = idx.shape[0]
+    st = KMeansState(ctx, n, K, device=idx.device, keep_dist=True)
+    work = torch.empty(max(256, sk.sk_kmeanspp_workspace_bytes(ctx, n)), dtype=torch.uint8,
+                       device=idx.device)
+    mu0 = torch.empty((K, ctx.pt), dtype=torch.float32, device=idx.device)
+    rows = torch.empty(K, dtype=torch.int64, device=idx.device)
+    J = torch.empty(1, dtype=torch.float64, device=idx.device)
+    best = None
+    for r in range(restarts):
+        sk.sk_kmeanspp(ctx, idx, val, K, restart=r, mu=mu0, rows=rows, work=work)
+        st.run(idx, val, mu0, iters, use_graph=use_graph)
+        # J' at the last assignment (the distances of the final labels)
+        sk.sk_kmeans_objective(st.dist, J=J)
+        j = float(J.item())
+        if best is None or j < best[2]:
+            best = (st.labels.clone(), st.mu.clone(), j, r)
+    return best
+
+
 def kmeans_2pass(ctx: sk.Ctx, X, labels1, mu_x, chunk_rows: int | None = None):
     """Second pass of Algorithm 2 over the raw rows X (n x p): labels against
     the un-mixed 1-pass centres mu_x (K x p) and the means of X under the
