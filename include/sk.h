@@ -317,8 +317,12 @@ sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_tota
  * (pt x pt float64) with its workspace gram_work (sk_cov_workspace_bytes of a
  * handle of the same p, m for `gram_mode` and n rows), and the K-means state
  * mu (K x pt float32), labels (n int32), S (K x pt float64), cnt (K x pt
- * int32), nk (K int64) and changed (one int64 or NULL).  All device buffers
- * are caller-owned and must stay valid while the batch is used.
+ * int32), nk (K int64) and changed (one int64 or NULL).  mu_t is optional
+ * scratch (device float32 pt x 2 ceil(K/2), or NULL): a data set whose
+ * centre table does not fit shared memory then reads a transposed copy of
+ * its centres kept there (one contiguous segment per sampled entry) instead
+ * of gathering each centre from mu.  All device buffers are caller-owned and
+ * must stay valid while the batch is used.
  *
  * Supported items: 4 <= p (pt >= 256 for the Gram: one tile shape per
  * launch), p % 4 == 0, ldx % 4 == 0 and X 16-byte aligned (rows staged with
@@ -337,6 +341,7 @@ typedef struct sk_batch_item {
     int64_t gram_work_bytes;
     int32_t K;
     float *mu;
+    float *mu_t;
     int32_t *labels;
     double *S;
     int32_t *cnt;

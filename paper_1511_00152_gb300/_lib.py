@@ -448,7 +448,7 @@ class SkBatchItem(ctypes.Structure):
                 ("ldx", ctypes.c_int64), ("row0", ctypes.c_int64), ("idx", ctypes.c_void_p),
                 ("val", ctypes.c_void_p), ("G", ctypes.c_void_p), ("gram_work", ctypes.c_void_p),
                 ("gram_work_bytes", ctypes.c_int64), ("K", ctypes.c_int32), ("mu", ctypes.c_void_p),
-                ("labels", ctypes.c_void_p), ("S", ctypes.c_void_p), ("cnt", ctypes.c_void_p),
+                ("mu_t", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("S", ctypes.c_void_p), ("cnt", ctypes.c_void_p),
                 ("nk", ctypes.c_void_p), ("changed", ctypes.c_void_p)]
 
 

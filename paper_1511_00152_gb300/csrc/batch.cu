@@ -34,8 +34,8 @@ static cudaError_t build_tables(sk_batch *B, int units_per_group, int gram_n) {
         const sk_batch_item &it = B->items[d];
         rows[d] = sk::BatchRows{it.X, it.n, it.ldx, it.row0, it.idx, it.val};
         grams[d] = sk::BatchGram{it.idx, it.val, it.n, it.G, it.gram_work};
-        kms[d] = sk::BatchKmeans{it.idx, it.val, it.n, it.K, it.mu, it.labels,
-                                 it.S,   it.cnt, it.nk, it.changed};
+        kms[d] = sk::BatchKmeans{it.idx, it.val, it.n,   it.K,  it.mu,
+                                 it.mu_t, it.labels, it.S, it.cnt, it.nk, it.changed};
         B->ctxs[d].gram_n = gram_n;
     }
     B->table.clear();

@@ -44,6 +44,7 @@ struct KmParams {
     int G;          // row slots per half-warp (0: rows laid out over the whole warp)
     int stage_cap;  // staged (idx, val) entries per warp
     const float *mu;
+    float *mu_t;  // batch only: transposed centres pt x Kpad in global memory (or NULL)
     int32_t *labels;
     float *dist;
     double *S;
@@ -377,7 +378,8 @@ __global__ void kmeans_finalize_kernel(int64_t KP, const double *S, const int32_
 // atomics (no shared-memory privatisation across data sets).
 struct KmTask {
     int32_t d;
-    int32_t variant;  // bit 0: centres in shared memory, bit 1: staged rows
+    int32_t variant;  // bit 0: centre table in shared memory, bit 1: staged rows,
+                      // bit 2: centre table = the transposed copy in global memory
     int64_t r_begin, r_end;
 };
 
@@ -412,6 +414,14 @@ __global__ void __launch_bounds__(kThreads, 1) kmeans_batch_kernel(const KmParam
         const int64_t base0 = T.r_begin + (int64_t)warp * P.RW;
         const int64_t step = (int64_t)kWarpsK * P.RW;
         switch (T.variant) {
+            case 6:
+                kmeans_rows<2, true, false, true, false>(P, P.mu_t, nullptr, nullptr, nullptr,
+                                                         stage_all, base0, step, T.r_end);
+                break;
+            case 4:
+                kmeans_rows<2, true, false, false, false>(P, P.mu_t, nullptr, nullptr, nullptr,
+                                                          stage_all, base0, step, T.r_end);
+                break;
             case 3:
                 kmeans_rows<2, true, false, true, false>(P, mus, nullptr, nullptr, nullptr,
                                                          stage_all, base0, step, T.r_end);
@@ -448,13 +458,21 @@ __global__ void kmeans_sums_batch_kernel(const KmParams *Ps, const int64_t *star
         }
         const KmParams &P = Ps[lo];
         const int64_t k = e - start[lo];
+        float *mu = const_cast<float *>(P.mu);
         if (mode == 0) {
             P.S[k] = 0.0;
             P.cnt[k] = 0;
             if (k < P.K) P.nk[k] = 0;
         } else {
             const int32_t c = P.cnt[k];
-            if (c > 0) const_cast<float *>(P.mu)[k] = (float)(P.S[k] / (double)c);
+            if (c > 0) mu[k] = (float)(P.S[k] / (double)c);
+        }
+        if (P.mu_t) {
+            // the transposed copy follows mu (and zero in the padding centre)
+            const int kk = (int)(k / P.pt), j = (int)(k - (int64_t)kk * P.pt);
+            P.mu_t[(int64_t)j * P.Kpad + kk] = mu[k];
+            if (mode == 0 && kk == P.K - 1)
+                for (int q = P.K; q < P.Kpad; ++q) P.mu_t[(int64_t)j * P.Kpad + q] = 0.f;
         }
     }
 }
@@ -587,6 +605,7 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
         P.G = P.LPR <= 16 ? 16 / P.LPR : 0;
         P.RW = P.G ? 2 * P.G : 32 / P.LPR;
         P.mu = it[d].mu;
+        P.mu_t = it[d].mu_t;
         P.labels = it[d].labels;
         P.dist = nullptr;
         P.S = it[d].S;
@@ -600,7 +619,7 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
         const bool staged = st_b <= stage_region;
         P.stage_cap = staged ? P.RW * P.m : 0;
         if (staged && st_b > stage_used) stage_used = st_b;
-        const int variant = (mu_smem ? 1 : 0) | (staged ? 2 : 0);
+        const int variant = (mu_smem ? 1 : (P.mu_t ? 4 : 0)) | (staged ? 2 : 0);
         const int64_t per = (int64_t)kWarpsK * P.RW * 16;  // 16 passes per warp
         for (int64_t r = 0; r < P.n; r += per) {
             KmTask T;

@@ -159,6 +159,7 @@ struct BatchKmeans {  // one data set's ELL rows and K-means state
     int64_t n;
     int K;
     float *mu;
+    float *mu_t;
     int32_t *labels;
     double *S;
     int32_t *cnt;

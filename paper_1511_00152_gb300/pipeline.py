@@ -174,6 +174,8 @@ class BatchRun:
             wb = sk.sk_cov_workspace_bytes(ctx, mode, n)
             e["work"] = torch.empty(max(wb, 256), dtype=torch.uint8, device=device)
             e["mu"] = torch.empty((K, pt), dtype=torch.float32, device=device)
+            # transposed centres (used when the table does not fit shared memory)
+            e["mu_t"] = torch.empty((pt, 2 * ((K + 1) // 2)), dtype=torch.float32, device=device)
             e["labels"] = torch.empty(n, dtype=torch.int32, device=device)
             e["S"] = torch.empty((K, pt), dtype=torch.float64, device=device)
             e["cnt"] = torch.empty((K, pt), dtype=torch.int32, device=device)
@@ -188,7 +190,8 @@ class BatchRun:
                 X=X.data_ptr(), n=n, ldx=X.stride(0) if n > 1 else p, row0=0,
                 idx=e["idx"].data_ptr(), val=e["val"].data_ptr(), G=e["G"].data_ptr(),
                 gram_work=e["work"].data_ptr(), gram_work_bytes=e["work"].numel(), K=K,
-                mu=e["mu"].data_ptr(), labels=e["labels"].data_ptr(), S=e["S"].data_ptr(),
+                mu=e["mu"].data_ptr(), mu_t=e["mu_t"].data_ptr(), labels=e["labels"].data_ptr(),
+                S=e["S"].data_ptr(),
                 cnt=e["cnt"].data_ptr(), nk=e["nk"].data_ptr(), changed=e["changed"].data_ptr()))
         self.batch = sk.sk_batch_create(items, mode, keep=self.ds)
         self.table = torch.empty(max(256, sk.sk_batch_workspace_bytes(self.batch)),
