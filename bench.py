@@ -429,7 +429,7 @@ def run_gpu(args, cfg):
     # the plain FP32 GPU form of the covariance pass (shared-memory scatter
     # Gram), timed beside the chosen mode on the same ELL rows
     plain = None
-    if mode != sk.SK_GRAM_FP32:
+    if mode != sk.SK_GRAM_FP32 and not args.no_plain:
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         sk.sk_cov_reset(ctx, G)
@@ -676,6 +676,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip timing the plain FP32 Gram beside the chosen mode")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the K-means loop kernel by kernel (for profilers)")
     ap.add_argument("--workload", default="kmeans", choices=["kmeans", "serving", "batching"],

@@ -614,7 +614,7 @@ int64_t gram_tc_workspace(const sk_ctx &c, int64_t n) {
 // precision stages, row splits, ring slot size and the workspace carve.
 static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const float *val,
                            int64_t n, double *G, void *work, TcParams &P, size_t &smem,
-                           int64_t &nslab) {
+                           int64_t &nslab, int stages_cap = 0) {
     if (c.pt < kTileM) return cudaErrorInvalidValue;
     P.idx = idx;
     P.val = val;
@@ -672,6 +672,17 @@ static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const 
     P.nsplits = (int)((n + rps - 1) / rps);
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // Dense rows (large m / pt) bring many entries per slab: a ring slot must
+    // hold one slab's A and B ranges (on average e = 64 m (128 + N) / pt
+    // entries of 8 bytes) or the producers fall back to scattered global
+    // reads.  Give up operand stages (down to two) until e plus four standard
+    // deviations (sqrt(e), the counts being near-binomial) fits a slot.
+    const double slab_entries = 64.0 * (double)c.m * (double)(kTileM + P.N) / (double)c.pt;
+    const int64_t need = (int64_t)((slab_entries + 4.0 * sqrt(slab_entries)) * 8.0) + 256;
+    while (P.nstages > 2 &&
+           ((int64_t)smem_max - (int64_t)P.nstages * P.stage_bytes - 1536) / kRing < need)
+        --P.nstages;
+    if (stages_cap > 0 && P.nstages > stages_cap) P.nstages = stages_cap;
     const size_t fixed = (size_t)P.nstages * P.stage_bytes + 1024 + 512;
     int64_t slot = ((int64_t)smem_max - (int64_t)fixed) / kRing;
     slot = slot / 16 * 16;
@@ -711,6 +722,18 @@ cudaError_t gram_batch_build(const sk_ctx *ctxs, const BatchGram *rows, int nd, 
     std::vector<int> slab_start((size_t)nd + 1), cta_start((size_t)nd + 1);
     int64_t slabs = 0, ctas = 0;
     size_t smem = 0;
+    // one launch has one operand pipeline: the shallowest any data set needs
+    int stages = 0;
+    for (int d = 0; d < nd; ++d) {
+        if (rows[d].n == 0) continue;
+        TcParams T;
+        size_t sm = 0;
+        int64_t nslab = 0;
+        cudaError_t e = tc_plan(ctxs[d], mode, rows[d].idx, rows[d].val, rows[d].n, rows[d].G,
+                                rows[d].work, T, sm, nslab);
+        if (e != cudaSuccess) return e;
+        if (stages == 0 || T.nstages < stages) stages = T.nstages;
+    }
     for (int d = 0; d < nd; ++d) {
         TcParams &P = Ps[d];
         size_t sm = 0;
@@ -723,7 +746,7 @@ cudaError_t gram_batch_build(const sk_ctx *ctxs, const BatchGram *rows, int nd, 
             continue;
         }
         cudaError_t e = tc_plan(ctxs[d], mode, rows[d].idx, rows[d].val, rows[d].n, rows[d].G,
-                                rows[d].work, P, sm, nslab);
+                                rows[d].work, P, sm, nslab, stages);
         if (e != cudaSuccess) return e;
         if (smem && (P.N != Ps[info.first].N || P.nstages != Ps[info.first].nstages ||
                      P.slot_bytes != Ps[info.first].slot_bytes))
