@@ -46,7 +46,12 @@ UNIT = "samples/s"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of this workload (profiles/), valid only
 # while the kernel source still has the digest it had when captured.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # profiles/kmeans_kernel_n4e5_p1024_K10.md: 164.92 MB read + 3.92 MB written
+    # per incremental pass at n = 400,000 (422.1 B per row), scaled to n = 10^6
+    "kmeans": {"bytes": 422_120_000, "n": 1_000_000, "p": 1024,
+               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "35716e1e0ad182e9"},
+}
 
 
 def source_digest(rel: str) -> str:
