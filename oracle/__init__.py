@@ -29,6 +29,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
   compress_raw    -- val = x[idx] with the (pinned) mask; raw padding is zero
   kmeans_2pass    -- brute-force dense distances and per-label means on small
                      inputs; converged Lloyd's is a fixed point (Algorithm 2)
+  kmeans_hk       -- m = pt gives H_k = I exactly; ||H_k - I|| within the
+                     matrix-Bernstein bound of Sec. VI-B (Thm. on H_k) at
+                     failure probability 1e-6; brute-force diagonal on tiny input
   kpp_draw        -- chi-square uniformity over [0, W); draws stay below W with
                      a rejection rate near 1/2 (W = 2^63 + 1)
   kmeanspp        -- first centre uniform over the rows (chi-square over
@@ -98,6 +101,7 @@ def _load():
             "oracle_kmeans_2pass": (None, [vp, i64, i64, vp, vp, i64, vp, vp, vp]),
             "oracle_kpp_draw": (u64, [u64, u32, u32, u64]),
             "oracle_kmeanspp": (None, [vp, vp, i64, i64, i64, i64, u64, u32, vp, vp]),
+            "oracle_kmeans_hk": (None, [vp, vp, i64, i64, i64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -328,6 +332,16 @@ def kmeanspp(idx, val, pt: int, K: int, seed: int, r: int = 0):
     _load().oracle_kmeanspp(_p(idx), _p(val), n, m, pt, K, int(seed) & (2**64 - 1), r,
                             _p(rows), _p(cen))
     return rows, cen
+
+
+def kmeans_hk(counts, nk, pt: int, m: int) -> np.ndarray:
+    """||H_k - I||_2 per cluster (Eq. (Hkmk)); -1 for an empty cluster."""
+    counts = _c(counts, np.int64)
+    nk = _c(nk, np.int64)
+    K = nk.shape[0]
+    dev = np.zeros(K, np.float64)
+    _load().oracle_kmeans_hk(_p(counts), _p(nk), K, pt, m, _p(dev))
+    return dev
 
 
 def unmix(M, p: int, seed: int) -> np.ndarray:

@@ -448,3 +448,22 @@ void oracle_kmeanspp(const int32_t *idx, const float *val, int64_t n, int64_t m,
     }
     free(D2);
 }
+
+/* ---------------- H_k of the centre update (Eq. (Hkmk)) ---------------- */
+
+/* dev[k] = || H_k - I ||_2 with H_k = (pt/m)(1/n_k) sum_{i in I_k} R_i R_i^T,
+ * a diagonal matrix whose entry j is (pt/m) counts[k][j] / nk[k]; -1 for an
+ * empty cluster (H_k undefined). */
+void oracle_kmeans_hk(const int64_t *counts, const int64_t *nk, int64_t K, int64_t pt,
+                      int64_t m, double *dev) {
+    for (int64_t k = 0; k < K; ++k) {
+        if (nk[k] == 0) { dev[k] = -1.0; continue; }
+        double worst = 0.0;
+        for (int64_t j = 0; j < pt; ++j) {
+            const double h = (double)pt / (double)m * (double)counts[k * pt + j] / (double)nk[k];
+            const double d = fabs(h - 1.0);
+            if (d > worst) worst = d;
+        }
+        dev[k] = worst;
+    }
+}

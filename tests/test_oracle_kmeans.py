@@ -144,3 +144,42 @@ def test_compress_raw_is_gather_of_padded_rows():
     for i in range(20):
         assert np.array_equal(idx[i], oracle.mask(64, 9, 3, 77 + i))
         assert np.array_equal(val[i], Xp[i, idx[i]])
+
+
+def test_hk_identity_at_full_sampling_and_brute_force():
+    """H_k = (pt/m)(1/n_k) sum_{i in I_k} R_i R_i^T (Eq. (Hkmk)): m = pt samples
+    every coordinate, so H_k = I exactly."""
+    n, p, K, seed = 500, 32, 3, 2
+    X = synth.uniform(n, p, seed=1)
+    pt = oracle.ptilde(p)
+    idx, val = oracle.compress(X, pt, seed)
+    labels = (np.arange(n) % K).astype(np.int32)
+    _mu, counts, nk = oracle.kmeans_update(idx, val, labels, np.zeros((K, pt)), pt)
+    assert np.array_equal(oracle.kmeans_hk(counts, nk, pt, pt), np.zeros(K))
+    # brute force on a tiny assignment, and an empty cluster
+    counts = np.array([[3, 1, 0, 2], [0, 0, 0, 0]], np.int64)
+    nk = np.array([3, 0], np.int64)
+    h = 4 / 2 * counts[0] / 3
+    dev = oracle.kmeans_hk(counts, nk, 4, 2)
+    assert abs(dev[0] - np.abs(h - 1).max()) < 1e-15 and dev[1] == -1.0
+
+
+def test_hk_within_matrix_bernstein_bound():
+    """Sec. VI-B: P(||H_k - I|| <= t) >= 1 - p exp(-(n_k t^2 / 2) /
+    ((p/m - 1) + (p/m + 1) t / 3)); the deviation must respect the t that
+    makes that failure probability 1e-6."""
+    n, p, m, K, seed = 40000, 64, 8, 2, 3
+    X = synth.uniform(n, p, seed=4)
+    pt = oracle.ptilde(p)
+    idx, val = oracle.compress(X, m, seed)
+    labels = (np.arange(n) % K).astype(np.int32)
+    _mu, counts, nk = oracle.kmeans_update(idx, val, labels, np.zeros((K, pt)), pt)
+    dev = oracle.kmeans_hk(counts, nk, pt, m)
+    r = pt / m
+    for k in range(K):
+        lo, hi = 0.0, 10.0
+        for _ in range(100):  # bisection for the t with failure probability 1e-6
+            t = 0.5 * (lo + hi)
+            d3 = pt * np.exp(-(nk[k] * t * t / 2) / ((r - 1) + (r + 1) * t / 3))
+            lo, hi = (t, hi) if d3 > 1e-6 else (lo, t)
+        assert 0.0 < dev[k] <= hi
