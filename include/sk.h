@@ -269,6 +269,14 @@ int64_t sk_kmeanspp_workspace_bytes(const sk_ctx *ctx, int64_t n);
  * objective). */
 sk_status sk_kmeans_objective(const float *dist, int64_t n, double *J, void *stream);
 
+/* Diagnostic of the centre update (Sec. VI-B, Eq. (Hkmk) and the theorem on
+ * H_k): dev[k] = || H_k - I ||_2 with H_k = (pt/m)(1/n_k) sum_{i in I_k}
+ * R_i R_i^T, diagonal with entries (pt/m) cnt[k*pt + j] / nk[k]; -1 for an
+ * empty cluster.  cnt, nk: the sums of sk_kmeans_update / step (device);
+ * dev: device float64 K. */
+sk_status sk_kmeans_hk(const sk_ctx *ctx, int32_t K, const int32_t *cnt, const int64_t *nk,
+                       double *dev, void *stream);
+
 /* Second pass of the 2-pass sparsified K-means (Algorithm 2), first half:
  * for each raw row x_i (X: device n x p float32, leading dimension ldx >= p),
  * labels[i] = argmin_k ||x_i - mu[k]||^2 over all p coordinates, ties to the

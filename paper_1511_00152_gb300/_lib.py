@@ -77,6 +77,7 @@ def load(path: str | None = None):
             "sk_kmeanspp": (st, [vp, vp, vp, i64, i32, ctypes.c_uint32, vp, vp, vp, i64, vp]),
             "sk_kmeanspp_workspace_bytes": (i64, [vp, i64]),
             "sk_kmeans_objective": (st, [vp, i64, vp, vp]),
+            "sk_kmeans_hk": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_mean_finalize": (st, [vp, vp, i64, vp, vp]),
             "sk_batch_create": (st, [ctypes.POINTER(vp), vp, i32, i32]),
             "sk_batch_workspace_bytes": (i64, [vp]),
@@ -419,6 +420,18 @@ def sk_kmeans_objective(dist, J=None, stream=None):
     _check("sk_kmeans_objective", load().sk_kmeans_objective(_ptr(dist), dist.numel(), _ptr(J),
                                                              _stream(stream)))
     return J
+
+
+def sk_kmeans_hk(ctx: Ctx, cnt, nk, dev=None, stream=None):
+    """||H_k - I||_2 per cluster (device float64 K; -1 for an empty cluster)."""
+    K = nk.shape[0]
+    _need(cnt, torch.int32, "cnt", (K, ctx.pt))
+    _need(nk, torch.int64, "nk", (K,))
+    if dev is None:
+        dev = torch.empty(K, dtype=torch.float64, device=nk.device)
+    _check("sk_kmeans_hk", load().sk_kmeans_hk(ctx.handle, K, _ptr(cnt), _ptr(nk), _ptr(dev),
+                                               _stream(stream)))
+    return dev
 
 
 def sk_mean_accumulate(ctx: Ctx, idx, val, sums, stream=None):

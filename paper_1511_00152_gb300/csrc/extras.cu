@@ -287,7 +287,36 @@ cudaError_t assign_launch(const sk_ctx &c, const float *X, int64_t n, int64_t ld
     return cudaGetLastError();
 }
 
+// ||H_k - I||_2 per cluster: H_k (Eq. (Hkmk)) is diagonal with entries
+// (pt/m) cnt[k][j] / n_k, so the norm is the largest |entry - 1|; -1 for an
+// empty cluster.  One CTA per cluster.
+__global__ void hk_kernel(const int32_t *cnt, const int64_t *nk, int pt, double ratio,
+                          double *dev) {
+    __shared__ double red[256];
+    const int k = blockIdx.x;
+    const int64_t n = nk[k];
+    double worst = 0.0;
+    if (n > 0)
+        for (int j = threadIdx.x; j < pt; j += blockDim.x) {
+            const double h = ratio * (double)cnt[(int64_t)k * pt + j] / (double)n;
+            worst = fmax(worst, fabs(h - 1.0));
+        }
+    red[threadIdx.x] = worst;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dev[k] = n > 0 ? red[0] : -1.0;
+}
+
 }  // namespace
+
+cudaError_t launch_kmeans_hk(const sk_ctx &c, int K, const int32_t *cnt, const int64_t *nk,
+                             double *dev, cudaStream_t s) {
+    hk_kernel<<<K, 256, 0, s>>>(cnt, nk, (int)c.pt, (double)c.pt / (double)c.m, dev);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_kmeans2_assign(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
                                   const float *mu, int K, int32_t *labels, float *dist,

@@ -341,6 +341,15 @@ sk_status sk_kmeans_objective(const float *dist, int64_t n, double *J, void *str
     return cuda_status(sk::launch_objective(dist, n, J, as_stream(stream)), "sk_kmeans_objective");
 }
 
+sk_status sk_kmeans_hk(const sk_ctx *ctx, int32_t K, const int32_t *cnt, const int64_t *nk,
+                       double *dev, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (K < 1 || K > 65535) return fail(SK_EINVAL, "sk_kmeans_hk: K out of range");
+    if (!cnt || !nk || !dev) return fail(SK_EINVAL, "sk_kmeans_hk: NULL buffer");
+    return cuda_status(sk::launch_kmeans_hk(*ctx, K, cnt, nk, dev, as_stream(stream)),
+                       "sk_kmeans_hk");
+}
+
 sk_status sk_kmeans2_assign(const sk_ctx *ctx, const float *X, int64_t n, int64_t ldx,
                             const float *mu, int32_t K, int32_t *labels, float *dist,
                             void *stream) {

@@ -201,6 +201,8 @@ cudaError_t launch_kmeanspp(const sk_ctx &c, const int32_t *idx, const float *va
                             int K, uint32_t restart, float *mu, int64_t *rows, void *work,
                             cudaStream_t s);
 cudaError_t launch_objective(const float *dist, int64_t n, double *J, cudaStream_t s);
+cudaError_t launch_kmeans_hk(const sk_ctx &c, int K, const int32_t *cnt, const int64_t *nk,
+                             double *dev, cudaStream_t s);
 // Algorithm 2's second pass and the sample mean (extras.cu).
 cudaError_t launch_kmeans2_assign(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
                                   const float *mu, int K, int32_t *labels, float *dist,

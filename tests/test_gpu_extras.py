@@ -232,3 +232,24 @@ def test_sample_mean_rejects_bad_args(sk):
     s = torch.zeros(ctx.pt, dtype=torch.float64, device="cuda")
     with pytest.raises(sk.SkError):
         sk.sk_mean_finalize(ctx, s, 0)
+
+
+def test_hk_deviation_matches_oracle(sk):
+    """||H_k - I|| (Sec. VI-B) from the GPU's sums against the oracle's on the
+    oracle's own rows and labels."""
+    n, p, m, K, seed = 6000, 256, 13, 5, 4
+    X = synth.uniform(n, p, seed=7)
+    ctx = sk.sk_init(p, m, seed)
+    oi, ov = oracle.compress(X, m, seed)
+    labels = (np.arange(n) % (K - 1)).astype(np.int32)  # cluster K-1 empty
+    _mu, counts_o, nk_o = oracle.kmeans_update(oi, ov, labels, np.zeros((K, ctx.pt)), ctx.pt)
+    ref = oracle.kmeans_hk(counts_o, nk_o, ctx.pt, m)
+    S = torch.zeros((K, ctx.pt), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros((K, ctx.pt), dtype=torch.int32, device="cuda")
+    nk = torch.zeros(K, dtype=torch.int64, device="cuda")
+    sk.sk_kmeans_update(ctx, _dev(oi), _dev(ov.astype(np.float32)), _dev(labels), K, S, cnt, nk)
+    dev = sk.sk_kmeans_hk(ctx, cnt, nk)
+    torch.cuda.synchronize()
+    assert np.array_equal(cnt.cpu().numpy(), counts_o)
+    assert np.abs(dev.cpu().numpy() - ref).max() <= 1e-14
+    assert dev[K - 1].item() == -1.0
