@@ -557,6 +557,95 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ PCA
+
+PCA = dict(workload="pca_lowrank_decay_n1048576_p4096_m205_k20", n=1_048_576, p=4096, m=205,
+           k=20, seed=7)
+
+
+def run_pca(args):
+    """Config 3: compress, then the three Gram paths on the same ELL rows
+    (split-BF16, BF16, plain FP32 scatter), C_n and the top-20 subspace.
+    Reports each path's time and tensor / HBM fraction, the split-BF16 and
+    BF16 Grams' relative Frobenius distance to the FP32 one (the FP64 oracle
+    itself is too slow at this size; the tests pin FP32 to it at smaller n),
+    and the eigen-residuals of the top-20 pairs."""
+    import torch
+    from paper_1511_00152_gb300 import build as skbuild
+    skbuild.build()
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import synth
+    cfg = dict(PCA)
+    n, p, m, k = cfg["n"], cfg["p"], cfg["m"], cfg["k"]
+    ctx = sk.sk_init(p, m, cfg["seed"])
+    pt = ctx.pt
+    X = synth.lowrank_decay_device(n, p, cfg["seed"])
+    idx = torch.empty((n, m), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    hbm, bf16, bf16s, src = load_peaks()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    reps = max(args.steps, 1) if args.steps <= 5 else 3
+    t_comp = timed(lambda: sk.sk_compress(ctx, X, idx=idx, val=val), reps)
+    del X
+    torch.cuda.empty_cache()
+    Gs, times = {}, {}
+    N = 256
+    ntiles = sum(pt // N - bi // (N // 128) for bi in range(pt // 128))
+    for name, mode in (("bf16x3", sk.SK_GRAM_BF16X3), ("bf16", sk.SK_GRAM_BF16),
+                       ("fp32", sk.SK_GRAM_FP32)):
+        G = torch.zeros((pt, pt), dtype=torch.float64, device="cuda")
+        wb = sk.sk_cov_workspace_bytes(ctx, mode, n)
+        work = torch.empty(max(wb, 256), dtype=torch.uint8, device="cuda")
+
+        def run(G=G, mode=mode, work=work):
+            sk.sk_cov_reset(ctx, G)
+            sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=work)
+        times[name] = timed(run, 1 if name == "fp32" else reps)
+        Gs[name] = G
+        del work
+    U32 = torch.triu(Gs["fp32"])
+    rel = {nm: float(torch.linalg.norm(torch.triu(Gs[nm]) - U32) / torch.linalg.norm(U32))
+           for nm in ("bf16x3", "bf16")}
+    C = sk.sk_cov_finalize(ctx, Gs["bf16x3"], n)
+    t_topk = timed(lambda: sk.sk_cov_topk(ctx, C, k, iters=20), 1)
+    ev, U = sk.sk_cov_topk(ctx, C, k, iters=20)
+    Cu = C @ U.T
+    res = float((torch.linalg.norm(Cu - U.T * ev[None, :], dim=0) / ev.abs()).max())
+    assert sk.sk_device_status() == sk.SK_OK
+    fl3 = 2.0 * n * 128 * N * ntiles * 3
+    line = {
+        "metric": "PCA workload: Gram paths (time, %tensor peak), rel-Frobenius vs FP32, top-20",
+        "value": n / ((t_comp + times["bf16x3"]) * 1e-3), "unit": "samples/s (compress + split-BF16 Gram)",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f32+bf16x3", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "n": n, "p": p, "m": m, "k": k},
+        "compress": {"ms": t_comp, "achieved_gbs": n * (4 * p + 8 * m) / (t_comp * 1e-3) / 1e9,
+                     "frac_hbm": n * (4 * p + 8 * m) / (t_comp * 1e-3) / 1e9 / hbm},
+        "gram_ms": times,
+        "gram_tflops_issued": {"bf16x3": fl3 / (times["bf16x3"] * 1e-3) / 1e12,
+                               "bf16": fl3 / 3 / (times["bf16"] * 1e-3) / 1e12},
+        "gram_frac_sustained_bf16": {"bf16x3": fl3 / (times["bf16x3"] * 1e-3) / 1e12 / bf16s,
+                                     "bf16": fl3 / 3 / (times["bf16"] * 1e-3) / 1e12 / bf16s},
+        "split_bf16_speedup_vs_fp32": times["fp32"] / times["bf16x3"],
+        "rel_frobenius_vs_fp32": rel,
+        "topk": {"ms": t_topk, "iters": 20, "max_rel_residual": res},
+        "peak_source": src,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ batching
 
 BATCHING = dict(workload="batch64_mixtures_p256-8192_n1e4-5e5", datasets=64, iters=15,
@@ -685,14 +774,17 @@ def main():
                     help="skip timing the plain FP32 Gram beside the chosen mode")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the K-means loop kernel by kernel (for profilers)")
-    ap.add_argument("--workload", default="kmeans", choices=["kmeans", "serving", "batching"],
+    ap.add_argument("--workload", default="kmeans",
+                    choices=["kmeans", "serving", "batching", "pca"],
                     help="kmeans: the main step (default); serving: the streaming request loop; "
-                         "batching: 64 data sets, one launch per stage")
+                         "batching: 64 data sets, one launch per stage; pca: the PCA workload")
     args = ap.parse_args()
     if args.workload == "serving" and args.impl != "reference":
         return run_serving(args)
     if args.workload == "batching" and args.impl != "reference":
         return run_batching(args)
+    if args.workload == "pca" and args.impl != "reference":
+        return run_pca(args)
     cfg = dict(WORKLOAD)
     if args.n:
         cfg["n"] = args.n
