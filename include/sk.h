@@ -144,13 +144,15 @@ sk_status sk_cov_finalize(const sk_ctx *ctx, const double *G, int64_t n_total,
  * float64), Sec. V PCA: eigenvalues (device float64, k, descending) and
  * eigenvectors (device float64, pt x k column-major, i.e. vector c at
  * U[c*pt .. c*pt+pt)) by block subspace iteration with Rayleigh-Ritz in
- * float64 on the device (the products with C and the final basis and
- * eigenproblem in float64; the intermediate re-orthonormalisations, which do
+ * float64 on the device (the last two products with C, the Rayleigh-Ritz
+ * product and the final basis and eigenproblem in float64; the earlier
+ * products in float32 and the intermediate re-orthonormalisations, which do
  * not change the iterated subspace, from float32 factors).  iters is the
  * number of iterations (0 is taken as 1); the subspace error shrinks by about
  * (lambda_{b+1} / lambda_k)^iters with b = min(pt, 64, max(k + 8, 2k)).
  * work is a device float64 scratch buffer of sk_cov_topk_workspace(pt, k)
- * doubles.  Requires 1 <= k <= min(pt, 64). */
+ * doubles.  C must be 16-byte aligned (SK_EINVAL otherwise).  Requires
+ * 1 <= k <= min(pt, 64). */
 sk_status sk_cov_topk(const sk_ctx *ctx, const double *C, int32_t k, int32_t iters,
                       double *evals, double *U, double *work, void *stream);
 int64_t sk_cov_topk_workspace(int64_t pt, int32_t k);

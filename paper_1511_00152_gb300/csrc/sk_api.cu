@@ -181,6 +181,8 @@ sk_status sk_cov_topk(const sk_ctx *ctx, const double *C, int32_t k, int32_t ite
         return fail(SK_EINVAL, "sk_cov_topk: k = %d must be in [1, min(pt, 64)]", k);
     if (iters < 0 || iters > 100000) return fail(SK_EINVAL, "sk_cov_topk: iters out of range");
     if (!C || !evals || !U || !work) return fail(SK_EINVAL, "sk_cov_topk: NULL buffer");
+    if (reinterpret_cast<uintptr_t>(C) % 16 != 0)
+        return fail(SK_EINVAL, "sk_cov_topk: C must be 16-byte aligned");
     return cuda_status(sk::launch_topk(*ctx, C, k, iters, evals, U, work, as_stream(stream)),
                        "sk_cov_topk");
 }
@@ -193,6 +195,8 @@ sk_status sk_cov_topk_static(const sk_ctx *ctx, const double *C, int32_t k, int3
     if (iters < 0 || iters > 100000)
         return fail(SK_EINVAL, "sk_cov_topk_static: iters out of range");
     if (!C || !evals || !U) return fail(SK_EINVAL, "sk_cov_topk_static: NULL buffer");
+    if (reinterpret_cast<uintptr_t>(C) % 16 != 0)
+        return fail(SK_EINVAL, "sk_cov_topk_static: C must be 16-byte aligned");
     const int64_t need = sk::topk_workspace(ctx->pt, k);
     const int64_t have = sk::topk_static_capacity();
     if (need > have)

@@ -6,7 +6,8 @@
 //   W = C V;  V = W R^{-1} with R the Cholesky factor of W^T W (CholQR),
 // repeated `iters` times (at least once) from a seeded start, the last
 // CholQR in float64 and the earlier ones from a float32 factor (see
-// chol32_kernel), then one Rayleigh-Ritz step:
+// chol32_kernel), the products C V of all but the last two iterations in
+// float32 (see panel_kernel), then one Rayleigh-Ritz step:
 // H = V^T C V (b x b), H = Q diag(lambda) Q^T, and U = V Q restricted to the
 // k largest lambda.  Each eigenvector's sign makes its largest-magnitude
 // entry positive.
@@ -68,44 +69,160 @@ __global__ void init_v_kernel(double *V, int64_t pt, int b, uint32_t k0, uint32_
 
 // W[c*pt + i] += sum_{j in this CTA's range} C[j*pt + i] V[c*pt + j], c < b
 // (C symmetric: row j read coalesced over i).  CTA = 128 columns i x one
-// j-range; a thread owns column i and its BC >= b accumulators; V's slice of
-// the j-range is staged in shared memory and read as a broadcast.  W is
-// zeroed before the launch and receives the partial sums with double atomics.
+// j-range; a thread owns column i and its BC >= b accumulators.  The j-range
+// goes in chunks of kPanelJ rows: the chunk's tile of C (kPanelJ x 128
+// doubles) is copied to shared memory with cp.async one chunk ahead of its
+// use (two buffers), and V's slice of the chunk is staged in shared memory
+// and read as a broadcast.  W is zeroed before the launch and receives the
+// partial sums with double atomics.
+// T is the arithmetic: double, or float for the early iterations (C, scaled
+// by 2^tshift, and V rounded to float as they are read, float products and
+// sums; W then holds 2^tshift C V), whose only job is to turn V towards the
+// dominant subspace.
 constexpr int kPanelThreads = 128;
-constexpr int kPanelJ = 32;
+constexpr int kPanelJ = 16;
 
-template <int BC>
-__global__ void __launch_bounds__(kPanelThreads) panel_kernel(const double *C, const double *V,
-                                                             int64_t pt, int b, int64_t jlen,
-                                                             double *W) {
-    __shared__ __align__(16) double Vs[kPanelJ][BC];
-    const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * kPanelThreads + tid;
-    const int64_t jb = (int64_t)blockIdx.y * jlen;
-    const int64_t je = (jb + jlen < pt) ? jb + jlen : pt;
-    double acc[BC];
-#pragma unroll
-    for (int c = 0; c < BC; ++c) acc[c] = 0.0;
-    for (int64_t j0 = jb; j0 < je; j0 += kPanelJ) {
-        const int jn = (int)((je - j0) < kPanelJ ? (je - j0) : kPanelJ);
-        for (int e = tid; e < kPanelJ * BC; e += kPanelThreads) {
-            const int jj = e / BC, c = e - jj * BC;
-            Vs[jj][c] = (jj < jn && c < b) ? V[(int64_t)c * pt + j0 + jj] : 0.0;
-        }
-        __syncthreads();
-        if (i < pt) {
-            for (int jj = 0; jj < jn; ++jj) {
-                const double cv = C[(j0 + jj) * pt + i];
-#pragma unroll
-                for (int c = 0; c < BC; ++c) acc[c] = fma(cv, Vs[jj][c], acc[c]);
-            }
-        }
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte global-to-shared copy of the first src_bytes (0..16) bytes of src,
+// zero-filling the rest (no byte is read when src_bytes is 0).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+// x * 2^t rounded toward zero to float, from the bit pattern of x on the
+// integer units (float64-to-float32 conversion instructions run at the low
+// float64 rate of this GPU).  Magnitudes below the float normal range
+// become zero; a result past the float range keeps the largest exponent.
+__device__ __forceinline__ float to_f32_rz(double x, int t) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127 + t;
+    const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    e = e > 254 ? 254 : e;
+    const uint32_t bits = (hi & 0x80000000u) | ((uint32_t)e << 23) | mant;
+    return e <= 0 ? 0.f : __uint_as_float(bits);
+}
+
+template <typename T>
+__device__ __forceinline__ T panel_in(double x, int t);
+template <>
+__device__ __forceinline__ double panel_in<double>(double x, int) { return x; }
+template <>
+__device__ __forceinline__ float panel_in<float>(double x, int t) { return to_f32_rz(x, t); }
+
+// *tshift = -(binary exponent of max_i |C_ii|): the float32 panels read C
+// scaled by 2^tshift, which puts the largest diagonal entry near 1 (the
+// scale cancels in the float32 CholQR, which normalises by the Gram's
+// diagonal).
+__global__ void __launch_bounds__(256) diag_shift_kernel(const double *C, int64_t pt,
+                                                        int *tshift) {
+    __shared__ int red[256];
+    int emax = 0;
+    for (int64_t i = threadIdx.x; i < pt; i += blockDim.x) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(C[i * pt + i]);
+        const int e = (int)((u >> 52) & 0x7FFu);
+        emax = e > emax ? e : emax;
+    }
+    red[threadIdx.x] = emax;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h && red[threadIdx.x + h] > red[threadIdx.x])
+            red[threadIdx.x] = red[threadIdx.x + h];
         __syncthreads();
     }
+    if (threadIdx.x == 0) *tshift = (red[0] == 0 || red[0] == 0x7FF) ? 0 : 1023 - red[0];
+}
+
+template <int BC, typename T>
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(const double *C, const double *V,
+                                                             int64_t pt, int b, int64_t jlen,
+                                                             const int *tshift, double *W) {
+    static_assert(kPanelThreads == 128 && kPanelJ % 2 == 0, "tile shape");
+    constexpr int VPT = (kPanelJ * BC + kPanelThreads - 1) / kPanelThreads;  // V loads / thread
+    __shared__ __align__(16) double Cs[2][kPanelJ][kPanelThreads];
+    __shared__ __align__(16) T Vs[2][kPanelJ][BC];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * kPanelThreads;
+    const int64_t jb = (int64_t)blockIdx.y * jlen;
+    const int64_t je = (jb + jlen < pt) ? jb + jlen : pt;
+    const int nch = (int)((je - jb + kPanelJ - 1) / kPanelJ);
+    const int tC = sizeof(T) == 4 ? *tshift : 0;
+
+    // C tile of chunk q: kPanelJ rows x 64 pieces of 16 bytes (two doubles)
+    auto issue_c = [&](int q) {
+        const int64_t j0 = jb + (int64_t)q * kPanelJ;
+#pragma unroll
+        for (int r = 0; r < kPanelJ * 64 / kPanelThreads; ++r) {
+            const int e = r * kPanelThreads + tid;
+            const int jj = e >> 6, seg = e & 63;
+            const int64_t j = j0 + jj, col = i0 + 2 * seg;
+            int bytes = 0;
+            if (j < je && col < pt) bytes = (pt - col >= 2) ? 16 : 8;
+            cp_async16(&Cs[q & 1][jj][2 * seg], bytes ? (const void *)(C + j * pt + col) : C,
+                       bytes);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // V slice of chunk q (consecutive threads: consecutive rows of a column)
+    auto load_v = [&](int q, T (&vr)[VPT]) {
+        const int64_t j0 = jb + (int64_t)q * kPanelJ;
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+            const int e = r * kPanelThreads + tid;
+            const int c = e / kPanelJ, jj = e - c * kPanelJ;
+            vr[r] = (e < kPanelJ * BC && c < b && j0 + jj < je)
+                        ? panel_in<T>(V[(int64_t)c * pt + j0 + jj], 0)
+                        : T(0);
+        }
+    };
+    auto store_v = [&](int q, const T (&vr)[VPT]) {
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+            const int e = r * kPanelThreads + tid;
+            const int c = e / kPanelJ, jj = e - c * kPanelJ;
+            if (e < kPanelJ * BC) Vs[q & 1][jj][c] = vr[r];
+        }
+    };
+
+    T acc[BC];
+#pragma unroll
+    for (int c = 0; c < BC; ++c) acc[c] = T(0);
+    if (nch > 0) {
+        T vr[VPT];
+        issue_c(0);
+        load_v(0, vr);
+        store_v(0, vr);
+    }
+    for (int q = 0; q < nch; ++q) {
+        T vr[VPT];
+        const bool more = q + 1 < nch;
+        if (more) {
+            issue_c(q + 1);
+            load_v(q + 1, vr);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < kPanelJ; ++jj) {
+            const T cv = panel_in<T>(Cs[q & 1][jj][tid], tC);
+#pragma unroll
+            for (int c = 0; c < BC; ++c) acc[c] = fma(cv, Vs[q & 1][jj][c], acc[c]);
+        }
+        if (more) store_v(q + 1, vr);
+        __syncthreads();
+    }
+    const int64_t i = i0 + tid;
     if (i < pt) {
 #pragma unroll
         for (int c = 0; c < BC; ++c)
-            if (c < b) atomicAdd(W + (int64_t)c * pt + i, acc[c]);
+            if (c < b) atomicAdd(W + (int64_t)c * pt + i, (double)acc[c]);
     }
 }
 
@@ -124,6 +241,32 @@ __global__ void small_gram_kernel(const double *A, const double *B, int64_t pt, 
         __syncthreads();
     }
     if (threadIdx.x == 0) Gm[blockIdx.x] = red[0];
+}
+
+// Gm += W^T W in float32 for the intermediate iterations, whose Gram only
+// feeds the float32 Cholesky of chol32_kernel.  A CTA takes a 64-row slice
+// of W (each element converted to float once, into shared memory) and adds
+// its b x b partial sums to Gm with double atomics; Gm starts at zero
+// (chol32_kernel clears it after reading it).
+constexpr int kG32Rows = 64;
+__global__ void __launch_bounds__(256) gram32_kernel(const double *W, int64_t pt, int b,
+                                                    double *Gm) {
+    __shared__ float Ws[kG32Rows][kMaxB + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * kG32Rows;
+    for (int e = threadIdx.x; e < kG32Rows * b; e += blockDim.x) {
+        const int c = e / kG32Rows, r = e - c * kG32Rows;
+        Ws[r][c] = (r0 + r < pt) ? (float)W[(int64_t)c * pt + r0 + r] : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int c1 = e / b, c2 = e - c1 * b;
+        if (c2 < c1) continue;
+        float s = 0.f;
+#pragma unroll 8
+        for (int r = 0; r < kG32Rows; ++r) s = fmaf(Ws[r][c1], Ws[r][c2], s);
+        atomicAdd(Gm + c1 * b + c2, (double)s);
+        if (c2 != c1) atomicAdd(Gm + c2 * b + c1, (double)s);
+    }
 }
 
 // In-place upper Cholesky G = R^T R of the SPD b x b matrix in shared memory
@@ -212,9 +355,9 @@ __global__ void __launch_bounds__(kApplyThreads) apply_solve_kernel(const double
 // diagonally scaled Gram S = D Gm D (D = diag(Gm)^{-1/2}, unit diagonal, so
 // float32 range is never an issue), M = D R_S^{-1}; V is then orthonormal
 // to float32 accuracy, and the last iteration re-orthonormalises in float64.
-__global__ void __launch_bounds__(256) chol32_kernel(const double *Gm, int b, double *Minv) {
-    __shared__ float A[kMaxB][kMaxB + 1];
-    __shared__ float X[kMaxB][kMaxB + 1];
+__global__ void __launch_bounds__(256) chol32_kernel(double *Gm, int b, double *Minv) {
+    __shared__ float A[kMaxB][kMaxB + 1];  // the scaled Gram, later X = R_S^{-1}
+    __shared__ float R[kMaxB][kMaxB + 1];  // R_S, upper
     __shared__ double d[kMaxB];
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int c = tid; c < b; c += nt) {
@@ -227,25 +370,28 @@ __global__ void __launch_bounds__(256) chol32_kernel(const double *Gm, int b, do
         A[r][c] = (float)(Gm[e] * d[r] * d[c]);
     }
     __syncthreads();
+    // Gm is read: clear it for the next iteration's gram32_kernel
+    for (int e = tid; e < b * b; e += nt) Gm[e] = 0.0;
+    // right-looking, one barrier per column: row c of R is written to R while
+    // the trailing update reads the unscaled row c of A and scales it itself
     for (int c = 0; c < b; ++c) {
-        if (tid == 0) A[c][c] = sqrtf(fmaxf(A[c][c], 1e-12f));
-        __syncthreads();
-        const float inv = 1.0f / A[c][c];
-        for (int j = c + 1 + tid; j < b; j += nt) A[c][j] *= inv;
-        __syncthreads();
+        const float rc = sqrtf(fmaxf(A[c][c], 1e-12f));
+        const float inv = 1.0f / rc;
+        for (int j = c + tid; j < b; j += nt) R[c][j] = (j == c) ? rc : A[c][j] * inv;
         const int rem = b - c - 1;
         for (int w = tid; w < rem * rem; w += nt) {
             const int i = c + 1 + w / rem, j = c + 1 + w % rem;
-            if (j >= i) A[i][j] -= A[c][i] * A[c][j];
+            if (j >= i) A[i][j] -= (A[c][i] * inv) * (A[c][j] * inv);
         }
         __syncthreads();
     }
-    // X = R_S^{-1} (upper) by back substitution, a thread per column
+    // X = R_S^{-1} (upper) by back substitution, a thread per column, into A
+    float (*X)[kMaxB + 1] = A;
     for (int j = tid; j < b; j += nt) {
         for (int i = j; i >= 0; --i) {
             float s = (i == j) ? 1.0f : 0.0f;
-            for (int q = i + 1; q <= j; ++q) s -= A[i][q] * X[q][j];
-            X[i][j] = s / A[i][i];
+            for (int q = i + 1; q <= j; ++q) s -= R[i][q] * X[q][j];
+            X[i][j] = s / R[i][i];
         }
     }
     __syncthreads();
@@ -278,8 +424,9 @@ __global__ void __launch_bounds__(256) apply_minv_kernel(const double *W, const 
 // decoupled zero row/column), bp - 1 steps per sweep; sweeps until the
 // off-diagonal mass is at most tol of the total.  Q accumulates the rotations.
 struct JacobiScratch {
-    int rp[kMaxB / 2], rq[kMaxB / 2];
+    unsigned char pp[kMaxB][kMaxB / 2], pq[kMaxB][kMaxB / 2];  // pair (p, q) of slot k at step s
     double rc[kMaxB / 2], rs[kMaxB / 2];
+    float rcf[kMaxB / 2], rsf[kMaxB / 2];
     double red[2][256];
     int done;
 };
@@ -321,6 +468,21 @@ __device__ void jacobi_dev(T (*A)[LDA], T (*Q)[LDQ], int b, int max_sweeps, doub
     const int tid = threadIdx.x, nt = blockDim.x;
     const int bp = (b + 1) & ~1;
     const int half = bp / 2;
+    // circle-method pairing of every step: index 0 fixed, 1..bp-1 rotate
+    for (int e = tid; e < (bp - 1) * half; e += nt) {
+        const int step = e / half, k = e - step * half;
+        int p, q;
+        if (k == 0) {
+            p = 0;
+            q = 1 + step % (bp - 1);
+        } else {
+            p = 1 + (step + k) % (bp - 1);
+            q = 1 + (step - k + (bp - 1)) % (bp - 1);
+        }
+        js.pp[step][k] = (unsigned char)p;
+        js.pq[step][k] = (unsigned char)q;
+    }
+    __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int e = tid; e < b * b; e += nt) {
@@ -344,49 +506,51 @@ __device__ void jacobi_dev(T (*A)[LDA], T (*Q)[LDQ], int b, int max_sweeps, doub
         if (js.done) break;
         for (int step = 0; step < bp - 1; ++step) {
             if (tid < half) {
-                // circle method: index 0 fixed, 1..bp-1 rotate
-                int p, q;
-                if (tid == 0) {
-                    p = 0;
-                    q = 1 + step % (bp - 1);
-                } else {
-                    p = 1 + (step + tid) % (bp - 1);
-                    q = 1 + (step - tid + (bp - 1)) % (bp - 1);
-                }
+                const int p = js.pp[step][tid], q = js.pq[step][tid];
                 double c = 1.0, sn = 0.0;
                 if (p < b && q < b) rot_params(A[p][p], A[q][q], A[p][q], c, sn);
-                js.rp[tid] = p;
-                js.rq[tid] = q;
                 js.rc[tid] = c;
                 js.rs[tid] = sn;
+                js.rcf[tid] = (float)c;
+                js.rsf[tid] = (float)sn;
             }
             __syncthreads();
-            // columns: A <- A J, Q <- Q J (a pair with the padding index is
-            // the identity)
-            for (int w = tid; w < half * bp; w += nt) {
-                const int k = w / bp, r = w - k * bp;
-                const int p = js.rp[k], q = js.rq[k];
-                if (p >= b || q >= b) continue;
-                const T c = (T)js.rc[k], sn = (T)js.rs[k];
-                const T arp = A[r][p], arq = A[r][q];
-                A[r][p] = c * arp - sn * arq;
-                A[r][q] = sn * arp + c * arq;
-                if (r < b) {
-                    const T qrp = Q[r][p], qrq = Q[r][q];
-                    Q[r][p] = c * qrp - sn * qrq;
-                    Q[r][q] = sn * qrp + c * qrq;
+            // A <- J^T A J on the 2 x 2 blocks (pair i rows, pair j columns):
+            // the blocks are disjoint, so each is updated on its own, the
+            // column rotation first, then the row rotation.  A pair with the
+            // padding index is the identity (its entries stay zero).
+            for (int w = tid; w < half * half; w += nt) {
+                const int ki = w / half, kj = w - ki * half;
+                const int p = js.pp[step][ki], q = js.pq[step][ki];
+                const int r = js.pp[step][kj], t = js.pq[step][kj];
+                T ci, si, cj, sj;
+                if constexpr (sizeof(T) == 4) {
+                    ci = js.rcf[ki]; si = js.rsf[ki]; cj = js.rcf[kj]; sj = js.rsf[kj];
+                } else {
+                    ci = js.rc[ki]; si = js.rs[ki]; cj = js.rc[kj]; sj = js.rs[kj];
                 }
+                const T apr = A[p][r], apt = A[p][t], aqr = A[q][r], aqt = A[q][t];
+                const T bpr = cj * apr - sj * apt, bpt = sj * apr + cj * apt;
+                const T bqr = cj * aqr - sj * aqt, bqt = sj * aqr + cj * aqt;
+                A[p][r] = ci * bpr - si * bqr;
+                A[q][r] = si * bpr + ci * bqr;
+                A[p][t] = ci * bpt - si * bqt;
+                A[q][t] = si * bpt + ci * bqt;
             }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int w = tid; w < half * bp; w += nt) {
-                const int k = w / bp, r = w - k * bp;
-                const int p = js.rp[k], q = js.rq[k];
+            // Q <- Q J
+            for (int w = tid; w < b * half; w += nt) {
+                const int row = w / half, k = w - row * half;
+                const int p = js.pp[step][k], q = js.pq[step][k];
                 if (p >= b || q >= b) continue;
-                const T c = (T)js.rc[k], sn = (T)js.rs[k];
-                const T apr = A[p][r], aqr = A[q][r];
-                A[p][r] = c * apr - sn * aqr;
-                A[q][r] = sn * apr + c * aqr;
+                T c, sn;
+                if constexpr (sizeof(T) == 4) {
+                    c = js.rcf[k]; sn = js.rsf[k];
+                } else {
+                    c = js.rc[k]; sn = js.rs[k];
+                }
+                const T qrp = Q[row][p], qrq = Q[row][q];
+                Q[row][p] = c * qrp - sn * qrq;
+                Q[row][q] = sn * qrp + c * qrq;
             }
             __syncthreads();
         }
@@ -425,8 +589,9 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b,
     }
     __syncthreads();
     // float32 Jacobi stalls near float32 rounding (off-diagonal mass around
-    // 1e-13 of the total), so it stops at 1e-10 or after 12 sweeps
-    jacobi_dev<float, kMaxB + 1, kMaxB>(S.A32, S.Q32, b, 12, 1e-10, S.js);
+    // 1e-13 of the total), so it stops at 1e-12 or after 15 sweeps; its
+    // sweeps cost a small fraction of a float64 sweep's
+    jacobi_dev<float, kMaxB + 1, kMaxB>(S.A32, S.Q32, b, 15, 1e-12, S.js);
     // G = Q32^T Q32 in float64
     for (int e = tid; e < b * b; e += nt) {
         const int i = e / b, j = e % b;
@@ -466,9 +631,12 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double *Hin, int b,
         if (r < b && c < b) S.Qb[r][c] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    // the polish starts from off-diagonal mass ~1e-10..1e-14 of the total;
-    // one or two sweeps reach 1e-26 (eigenvector directions to ~1e-13 / gap)
-    jacobi_dev<double, kMaxB + 1, kMaxB>(S.A64, S.Qb, b, 30, 1e-26, S.js);
+    // the polish starts from off-diagonal mass ~1e-12..1e-14 of the total;
+    // a sweep with float32-estimated angles shrinks it by ~1e-13 or more, so
+    // one sweep normally reaches 1e-20 (off-diagonal norm 1e-10 of the
+    // total: eigenvalues to ~1e-20 relative, eigenvector directions to
+    // ~1e-10 / relative gap)
+    jacobi_dev<double, kMaxB + 1, kMaxB>(S.A64, S.Qb, b, 30, 1e-20, S.js);
     for (int e = tid; e < b * b; e += nt) {
         const int r = e / b, c = e % b;
         double s = 0.0;
@@ -590,22 +758,25 @@ int64_t topk_workspace(int64_t pt, int k) {
 
 template <int BC>
 cudaError_t panel_launch(dim3 grid, const double *C, const double *V, int64_t pt, int b,
-                         int64_t jlen, double *W, cudaStream_t s) {
-    panel_kernel<BC><<<grid, kPanelThreads, 0, s>>>(C, V, pt, b, jlen, W);
+                         int64_t jlen, const int *tshift, double *W, bool f32, cudaStream_t s) {
+    if (f32)
+        panel_kernel<BC, float><<<grid, kPanelThreads, 0, s>>>(C, V, pt, b, jlen, tshift, W);
+    else
+        panel_kernel<BC, double><<<grid, kPanelThreads, 0, s>>>(C, V, pt, b, jlen, tshift, W);
     return cudaGetLastError();
 }
 
 cudaError_t panel(dim3 grid, const double *C, const double *V, int64_t pt, int b, int64_t jlen,
-                  double *W, cudaStream_t s) {
+                  const int *tshift, double *W, bool f32, cudaStream_t s) {
     switch ((b + 7) / 8) {
-        case 1: return panel_launch<8>(grid, C, V, pt, b, jlen, W, s);
-        case 2: return panel_launch<16>(grid, C, V, pt, b, jlen, W, s);
-        case 3: return panel_launch<24>(grid, C, V, pt, b, jlen, W, s);
-        case 4: return panel_launch<32>(grid, C, V, pt, b, jlen, W, s);
-        case 5: return panel_launch<40>(grid, C, V, pt, b, jlen, W, s);
-        case 6: return panel_launch<48>(grid, C, V, pt, b, jlen, W, s);
-        case 7: return panel_launch<56>(grid, C, V, pt, b, jlen, W, s);
-        default: return panel_launch<64>(grid, C, V, pt, b, jlen, W, s);
+        case 1: return panel_launch<8>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        case 2: return panel_launch<16>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        case 3: return panel_launch<24>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        case 4: return panel_launch<32>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        case 5: return panel_launch<40>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        case 6: return panel_launch<48>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        case 7: return panel_launch<56>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
+        default: return panel_launch<64>(grid, C, V, pt, b, jlen, tshift, W, f32, s);
     }
 }
 
@@ -618,11 +789,12 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // panel grid: 128-column tiles times j-ranges (multiples of 32 rows),
-    // about two CTAs per SM
+    // panel grid: 128-column tiles times j-ranges (multiples of kPanelJ
+    // rows, at least four chunks), about four CTAs per SM
     const int64_t itiles = (pt + kPanelThreads - 1) / kPanelThreads;
-    int64_t jsplit = (2LL * sms + itiles - 1) / itiles;
-    if (jsplit > (pt + kPanelJ - 1) / kPanelJ) jsplit = (pt + kPanelJ - 1) / kPanelJ;
+    int64_t jsplit = (4LL * sms + itiles - 1) / itiles;
+    const int64_t jmax = (pt + 4 * kPanelJ - 1) / (4 * kPanelJ);
+    if (jsplit > jmax) jsplit = jmax;
     if (jsplit < 1) jsplit = 1;
     int64_t jlen = (pt + jsplit - 1) / jsplit;
     jlen = (jlen + kPanelJ - 1) / kPanelJ * kPanelJ;
@@ -643,20 +815,30 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     if (mblocks > 4 * sms) mblocks = 4 * sms;
     int ublocks = (int)((k * pt + 255) / 256);
     if (ublocks > 4 * sms) ublocks = 4 * sms;
-    // at least one CholQR, the last one in float64
+    // at least one CholQR, the last one in float64; the last three panel
+    // products (two power steps and the Rayleigh-Ritz product) in float64,
+    // the earlier ones in float32: each float64 step shrinks the float32
+    // rounding left in span(V) by the gap ratio lambda_{b+1} / lambda_k.
     const int n_it = iters > 0 ? iters : 1;
+    const unsigned g32blocks = (unsigned)((pt + kG32Rows - 1) / kG32Rows);
     init_v_kernel<<<eblocks, 256, 0, s>>>(w.V, pt, b, k0, k1);
+    e = cudaMemsetAsync(w.Gm, 0, (size_t)b * b * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    // H is free until the Rayleigh-Ritz step: it holds the float32 panels' shift
+    int *tshift = reinterpret_cast<int *>(w.H);
+    if (n_it > 2) diag_shift_kernel<<<1, 256, 0, s>>>(C, pt, tshift);
     for (int it = 0; it <= n_it; ++it) {
         e = cudaMemsetAsync(w.W, 0, (size_t)b * pt * sizeof(double), s);
         if (e != cudaSuccess) return e;
-        e = panel(pgrid, C, w.V, pt, b, jlen, w.W, s);
+        e = panel(pgrid, C, w.V, pt, b, jlen, tshift, w.W, it < n_it - 2, s);
         if (e != cudaSuccess) return e;
         if (it == n_it) break;
-        small_gram_kernel<<<b * b, 256, 0, s>>>(w.W, w.W, pt, b, w.Gm);
         if (it < n_it - 1) {
+            gram32_kernel<<<g32blocks, 256, 0, s>>>(w.W, pt, b, w.Gm);
             chol32_kernel<<<1, 256, 0, s>>>(w.Gm, b, w.R);
             apply_minv_kernel<<<mblocks, 256, 0, s>>>(w.W, w.R, pt, b, w.V);
         } else {
+            small_gram_kernel<<<b * b, 256, 0, s>>>(w.W, w.W, pt, b, w.Gm);
             chol_kernel<<<1, 256, 0, s>>>(w.Gm, b, w.R, w.lam);
             apply_solve_kernel<<<ablocks, kApplyThreads, apply_smem, s>>>(w.W, w.R, w.lam, pt,
                                                                           b, w.V);
