@@ -111,8 +111,8 @@ def lowrank_decay_device(n: int, p: int, seed: int, rank: int = 20, noise: float
     import torch
     g = _torch_gen(seed, device)
     G = torch.randn(p, rank, generator=g, device=device, dtype=torch.float64)
-    Q, _ = torch.linalg.qr(G)
-    Q = Q.to(torch.float32)
+    Q, _ = torch.linalg.qr(G.cpu())  # p x rank: small, on the host
+    Q = Q.to(device=device, dtype=torch.float32)
     sv = (scale / torch.arange(1, rank + 1, device=device, dtype=torch.float32))
     X = torch.empty(n, p, device=device, dtype=torch.float32)
     for r0 in range(0, n, chunk):
