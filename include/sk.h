@@ -334,9 +334,10 @@ sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_tota
  * of gathering each centre from mu.  All device buffers are caller-owned and
  * must stay valid while the batch is used.
  *
- * Supported items: 4 <= p (pt >= 256 for the Gram: one tile shape per
- * launch), p % 4 == 0, ldx % 4 == 0 and X 16-byte aligned (rows staged with
- * bulk copies), 1 <= K <= 64.  Other items are rejected by sk_batch_create
+ * Supported items: 4 <= p (pt >= 256), p % 4 == 0, ldx % 4 == 0 and X
+ * 16-byte aligned (rows staged with bulk copies), 1 <= K <= 64.  Within one
+ * launch every data set keeps its own tensor-core Gram plan (operand stages
+ * and ring slot size from its density).  Other items are rejected by sk_batch_create
  * with SK_EUNSUPPORTED or SK_EINVAL. */
 typedef struct sk_batch_item {
     int64_t p, m;

@@ -614,7 +614,7 @@ int64_t gram_tc_workspace(const sk_ctx &c, int64_t n) {
 // precision stages, row splits, ring slot size and the workspace carve.
 static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const float *val,
                            int64_t n, double *G, void *work, TcParams &P, size_t &smem,
-                           int64_t &nslab, int stages_cap = 0) {
+                           int64_t &nslab) {
     if (c.pt < kTileM) return cudaErrorInvalidValue;
     P.idx = idx;
     P.val = val;
@@ -682,7 +682,6 @@ static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const 
     while (P.nstages > 2 &&
            ((int64_t)smem_max - (int64_t)P.nstages * P.stage_bytes - 1536) / kRing < need)
         --P.nstages;
-    if (stages_cap > 0 && P.nstages > stages_cap) P.nstages = stages_cap;
     const size_t fixed = (size_t)P.nstages * P.stage_bytes + 1024 + 512;
     int64_t slot = ((int64_t)smem_max - (int64_t)fixed) / kRing;
     slot = slot / 16 * 16;
@@ -722,18 +721,9 @@ cudaError_t gram_batch_build(const sk_ctx *ctxs, const BatchGram *rows, int nd, 
     std::vector<int> slab_start((size_t)nd + 1), cta_start((size_t)nd + 1);
     int64_t slabs = 0, ctas = 0;
     size_t smem = 0;
-    // one launch has one operand pipeline: the shallowest any data set needs
-    int stages = 0;
-    for (int d = 0; d < nd; ++d) {
-        if (rows[d].n == 0) continue;
-        TcParams T;
-        size_t sm = 0;
-        int64_t nslab = 0;
-        cudaError_t e = tc_plan(ctxs[d], mode, rows[d].idx, rows[d].val, rows[d].n, rows[d].G,
-                                rows[d].work, T, sm, nslab);
-        if (e != cudaSuccess) return e;
-        if (stages == 0 || T.nstages < stages) stages = T.nstages;
-    }
+    // Each data set keeps its own plan (tile width, operand stages, ring slot
+    // size): a CTA carves its shared memory from its data set's parameters,
+    // and the launch provides the largest plan's size.
     for (int d = 0; d < nd; ++d) {
         TcParams &P = Ps[d];
         size_t sm = 0;
@@ -746,13 +736,10 @@ cudaError_t gram_batch_build(const sk_ctx *ctxs, const BatchGram *rows, int nd, 
             continue;
         }
         cudaError_t e = tc_plan(ctxs[d], mode, rows[d].idx, rows[d].val, rows[d].n, rows[d].G,
-                                rows[d].work, P, sm, nslab, stages);
+                                rows[d].work, P, sm, nslab);
         if (e != cudaSuccess) return e;
-        if (smem && (P.N != Ps[info.first].N || P.nstages != Ps[info.first].nstages ||
-                     P.slot_bytes != Ps[info.first].slot_bytes))
-            return cudaErrorInvalidValue;  // one launch needs one tile shape
         if (!smem) info.first = d;
-        smem = sm;
+        if (sm > smem) smem = sm;
         Bs[d] = BucketParams{rows[d].idx, rows[d].val, rows[d].n, P.m, P.pt, P.nblk,
                              const_cast<int2 *>(P.bkt), const_cast<int *>(P.boff)};
         slabs += nslab;
