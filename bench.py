@@ -389,15 +389,15 @@ def run_gpu(args, cfg):
         lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
         cen_h = torch.empty((K, p), dtype=torch.float32, pin_memory=True)
         ux_h = torch.empty((k, p), dtype=torch.float64, pin_memory=True)
-        Xd2 = torch.empty_like(X)
         Xsel2 = torch.empty_like(Xsel)
+        # X streams to the device in chunks; each chunk is compressed and added
+        # to the Gram while the next ones are copied (a ring of three chunk
+        # buffers on the device)
+        streamer = pipeline.HostStreamer(ctx, (n + 7) // 8, mode, nbuf=3, device=dev)
 
         def e2e_step():
-            Xd2.copy_(Xh, non_blocking=True)
             Xsel2.copy_(Xsel_h, non_blocking=True)
-            sk.sk_compress(ctx, Xd2, idx=idx, val=val)
-            sk.sk_cov_reset(ctx, G)
-            sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=gwork)
+            streamer.run(Xh, idx, val, G)
             sk.sk_cov_finalize(ctx, G, n, C=C)
             sk.sk_cov_topk(ctx, C, k, args.topk_iters, evals=evals, U=U, work=work)
             sk.sk_unmix(ctx, U, out=Ux)

@@ -143,6 +143,75 @@ def covariance(ctx: sk.Ctx, idx, val, mode: int, G=None, C=None, work=None):
     return sk.sk_cov_finalize(ctx, G, idx.shape[0], C=C)
 
 
+class HostStreamer:
+    """Compress host rows and add them to the Gram while they stream to the
+    device (Algorithm 1's one pass over X, Sec. V's G = sum of w w^T).
+
+    Xh is pinned host memory (n x p float32).  The rows go to the device in
+    chunks on a copy stream, into a ring of `nbuf` device chunk buffers; the
+    caller's stream compresses each chunk into its rows of the ELL output and
+    adds it to G as soon as it has landed, so the copy of the next chunks
+    overlaps this work.  The masks are keyed by the global row number (row0 of
+    each chunk), so idx / val are those of one sk_compress call over all n
+    rows; G equals the one-call Gram up to float64 summation order.
+
+    Stream order: the compute of chunk c waits for the copy of chunk c; the
+    copy into a ring buffer waits for the compute of the chunk that used it
+    before, in this call or an earlier one (so a call may be enqueued while
+    the previous one still runs: its first copies then overlap the caller's
+    work that follows the previous call).  Each wait is issued after the
+    record it waits for and before that event is recorded again, so no wait
+    depends on work queued after it.
+    """
+
+    def __init__(self, ctx: sk.Ctx, chunk_rows: int, mode: int, nbuf: int = 3,
+                 device="cuda"):
+        if chunk_rows < 1 or nbuf < 1:
+            raise ValueError("chunk_rows and nbuf must be positive")
+        self.ctx, self.mode, self.chunk = ctx, mode, int(chunk_rows)
+        self.bufs = [torch.empty((self.chunk, ctx.p), dtype=torch.float32, device=device)
+                     for _ in range(nbuf)]
+        self.copy_stream = torch.cuda.Stream(device=device)
+        self.copied = [torch.cuda.Event() for _ in range(nbuf)]
+        self.used = [torch.cuda.Event() for _ in range(nbuf)]
+        self.used_recorded = [False] * nbuf
+        need = sk.sk_cov_workspace_bytes(ctx, mode, self.chunk)
+        self.work = torch.empty(max(1, need), dtype=torch.uint8, device=device)
+
+    def run(self, Xh, idx, val, G, reset: bool = True):
+        """Streams Xh through compress and the Gram update; returns G."""
+        if Xh.is_cuda or not Xh.is_pinned():
+            raise ValueError("Xh must be pinned host memory")
+        n = Xh.shape[0]
+        stream = torch.cuda.current_stream()
+        nb, ch = len(self.bufs), self.chunk
+        nch = (n + ch - 1) // ch
+        if reset:
+            sk.sk_cov_reset(self.ctx, G)
+
+        def issue(c):
+            r0, r1, b = c * ch, min(n, (c + 1) * ch), c % nb
+            with torch.cuda.stream(self.copy_stream):
+                if self.used_recorded[b]:
+                    self.copy_stream.wait_event(self.used[b])
+                self.bufs[b][: r1 - r0].copy_(Xh[r0:r1], non_blocking=True)
+                self.copied[b].record(self.copy_stream)
+
+        for c in range(min(nb, nch)):
+            issue(c)
+        for c in range(nch):
+            r0, r1, b = c * ch, min(n, (c + 1) * ch), c % nb
+            stream.wait_event(self.copied[b])
+            sk.sk_compress(self.ctx, self.bufs[b][: r1 - r0], row0=r0, idx=idx[r0:r1],
+                           val=val[r0:r1])
+            sk.sk_cov_accumulate(self.ctx, self.mode, idx[r0:r1], val[r0:r1], G, work=self.work)
+            self.used[b].record(stream)
+            self.used_recorded[b] = True
+            if c + nb < nch:
+                issue(c + nb)
+        return G
+
+
 def pca(ctx: sk.Ctx, C, k: int, iters: int = 40):
     """Top-k eigenpairs of C_n and the eigenvectors un-mixed to the data domain
     (U = (HD)^T U', Sec. V).  Returns (evals, U' [k x pt], U [k x p])."""

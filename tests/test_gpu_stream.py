@@ -1,0 +1,62 @@
+"""Host-streamed compress + Gram (pipeline.HostStreamer) against the one-call
+path on the same rows: the ELL output is bit-identical (masks keyed by the
+global row, Algorithm 1's one pass), and G equals the one-call Gram up to the
+float64 summation order of its chunks (Sec. V)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sk():
+    from paper_1511_00152_gb300 import build
+    build.build()
+    from paper_1511_00152_gb300 import _lib
+    return _lib
+
+
+@pytest.mark.parametrize("mode_name,chunk,nbuf", [("bf16x3", 7000, 2), ("fp32", 12345, 3),
+                                                  ("bf16x3", 60000, 3)])
+def test_streamed_equals_one_call(sk, mode_name, chunk, nbuf):
+    from paper_1511_00152_gb300 import pipeline
+    mode = {"bf16x3": sk.SK_GRAM_BF16X3, "fp32": sk.SK_GRAM_FP32}[mode_name]
+    n, p, m, seed = 50_001, 300, 20, 11
+    rng = np.random.default_rng(5)
+    Xh = torch.from_numpy(rng.standard_normal((n, p)).astype(np.float32)).pin_memory()
+    ctx = sk.sk_init(p, m, seed)
+    pt = ctx.pt
+    idx = torch.empty((n, m), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    G = torch.empty((pt, pt), dtype=torch.float64, device="cuda")
+    st = pipeline.HostStreamer(ctx, chunk, mode, nbuf=nbuf)
+    st.run(Xh, idx, val, G)
+    torch.cuda.synchronize()
+    Xd = Xh.cuda()
+    i1, v1 = sk.sk_compress(ctx, Xd)
+    G1 = torch.empty_like(G)
+    sk.sk_cov_reset(ctx, G1)
+    sk.sk_cov_accumulate(ctx, mode, i1, v1, G1)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, i1)
+    assert torch.equal(val, v1)
+    U, U1 = torch.triu(G), torch.triu(G1)
+    rel = float(((U - U1) ** 2).sum().sqrt() / (U1 ** 2).sum().sqrt())
+    assert rel <= 1e-6, rel
+    # streaming twice into the same buffers gives the same result
+    G2 = torch.empty_like(G)
+    st.run(Xh, idx, val, G2)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, i1)
+    assert float(((torch.triu(G2) - U) ** 2).sum().sqrt() / (U1 ** 2).sum().sqrt()) <= 1e-6
+    assert sk.sk_device_status() == sk.SK_OK
+
+
+def test_streamer_rejects_device_input(sk):
+    from paper_1511_00152_gb300 import pipeline
+    ctx = sk.sk_init(64, 8, 1)
+    st = pipeline.HostStreamer(ctx, 100, sk.SK_GRAM_FP32, nbuf=2)
+    X = torch.zeros((10, 64), device="cuda")
+    with pytest.raises(ValueError):
+        st.run(X, None, None, None)
