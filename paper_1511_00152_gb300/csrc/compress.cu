@@ -207,8 +207,8 @@ __device__ __forceinline__ void ensure_batches(WordWindow &ww, const CompressPar
     }
 }
 
-// Mask of one row and its ELL gather, by one warp.
-template <int L>
+// Mask of one row and (GATHER) its ELL gather, by one warp.
+template <int L, bool GATHER = true>
 __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
                                            const float *ybuf, int ebase, uint32_t *A,
                                            uint32_t *hit, uint32_t *words, uint32_t tag, int lane) {
@@ -271,7 +271,7 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
             A[k] = (tag << 16) | (uint32_t)V;
         if (act) {
             oidx[t] = omega;
-            oval[t] = ybuf[yaddr<L>(ebase, omega)] * P.scale;
+            if constexpr (GATHER) oval[t] = ybuf[yaddr<L>(ebase, omega)] * P.scale;
         }
         __syncwarp();
     }
@@ -283,14 +283,15 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
 // group, the staging buffers, the virtual Fisher-Yates array and the hit table.
 constexpr size_t kFixedSmem = (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4;
 
-template <int L, bool TMA>
+template <int L, bool TMA, bool SPLIT = false>
 constexpr size_t compress_smem_bytes() {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;
     constexpr int NG = kWarps / G;
     constexpr int BUF = (L <= 10) ? 1024 : PT;
     constexpr int NBUF = TMA ? kNB : 1;
-    return kFixedSmem + (size_t)NG * NBUF * BUF * 4 + (size_t)NG * PT * 4 + (size_t)NG * 32 * 4;
+    constexpr int NA = SPLIT ? 0 : PT;  // the mask kernel holds the Fisher-Yates arrays
+    return kFixedSmem + (size_t)NG * NBUF * BUF * 4 + (size_t)NG * NA * 4 + (size_t)NG * 32 * 4;
 }
 
 __device__ __forceinline__ void init_unit_barriers(unsigned char *smem_raw) {
@@ -307,8 +308,10 @@ __device__ __forceinline__ void init_unit_barriers(unsigned char *smem_raw) {
 // set described by P: a unit is RPU rows (pt <= 1024, one warp each) or one
 // row (pt > 1024, G warps).  kloc counts the units this warp has staged
 // through its two TMA buffers (it carries the buffer / barrier-phase
-// sequence across calls).  Returns false if a bounded wait ran out.
-template <int L, bool DENSE, bool TMA>
+// sequence across calls).  SPLIT (pt > 1024): the masks are already in
+// P.idx (mask_kernel) and all G warps of the row share its gather.  Returns
+// false if a bounded wait ran out.
+template <int L, bool DENSE, bool TMA, bool SPLIT = false>
 __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t u0,
                                                int64_t stride, int64_t u_end,
                                                unsigned char *smem_raw, int64_t &kloc) {
@@ -327,9 +330,10 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
     float *ybuf = ybufs;
     unsigned char *after = var + (size_t)NG * NBUF * BUF * 4;
     uint32_t *A = reinterpret_cast<uint32_t *>(after) + grp * PT;
-    uint32_t *hit = reinterpret_cast<uint32_t *>(after + (size_t)NG * PT * 4) + grp * 32;
+    uint32_t *hit = reinterpret_cast<uint32_t *>(after + (size_t)NG * (SPLIT ? 0 : PT) * 4) + grp * 32;
+    static_assert(!SPLIT || (L > 10 && !DENSE), "split masks: pt > 1024, ELL output");
 
-    if constexpr (!DENSE) {
+    if constexpr (!DENSE && !SPLIT) {
         if (wg == 0)
             for (int j = lane; j < PT; j += 32) A[j] = 0u;
     }
@@ -513,6 +517,15 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
                     if (i < P.n) P.Y[i * PT + c] = ys[q] * P.scale;
                 }
             }
+        } else if constexpr (SPLIT) {
+            // one row: its m entries are shared by the G warps of the group
+            if (r0 < P.n) {
+                const int m = P.m;
+                const int32_t *gi = P.idx + r0 * (int64_t)m;
+                float *ov = P.val + r0 * (int64_t)m;
+                for (int t = wg * 32 + lane; t < m; t += G * 32)
+                    ov[t] = ybuf[yaddr<L>(0, __ldcg(gi + t) & (PT - 1))] * P.scale;
+            }
         } else {
             if (L <= 10 || wg == 0) {
 #pragma unroll 1
@@ -532,7 +545,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
     return ok;
 }
 
-template <int L, bool DENSE, bool TMA>
+template <int L, bool DENSE, bool TMA, bool SPLIT = false>
 __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams P) {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;
@@ -542,18 +555,74 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
     if constexpr (TMA) init_unit_barriers(smem_raw);
     const int64_t nunits = (L <= 10) ? (P.n + RPU - 1) / RPU : P.n;
     int64_t kloc = 0;
-    compress_units<L, DENSE, TMA>(P, (int64_t)blockIdx.x * NG, (int64_t)gridDim.x * NG, nunits,
-                                  smem_raw, kloc);
+    compress_units<L, DENSE, TMA, SPLIT>(P, (int64_t)blockIdx.x * NG, (int64_t)gridDim.x * NG,
+                                         nunits, smem_raw, kloc);
 }
 
-template <int L, bool DENSE, bool TMA>
+// Masks only (pt > 1024): every warp draws whole rows on its own (its own
+// virtual Fisher-Yates array and word window) and writes idx; the transform
+// kernel then gathers val with all the warps of a row group.  At pt > 1024 a
+// row's transform takes G = pt / 1024 warps, and drawing its mask on one of
+// them left the other G - 1 waiting.
+template <int L>
+__host__ __device__ constexpr int mask_warps() { return L >= 13 ? 2 : 4; }
+
+template <int L>
+constexpr size_t mask_smem_bytes() {
+    return (size_t)mask_warps<L>() * (256 * 4 + (1 << L) * 4 + 32 * 4);
+}
+
+template <int L>
+__global__ void __launch_bounds__(mask_warps<L>() * 32) mask_kernel(CompressParams P) {
+    constexpr int PT = 1 << L;
+    constexpr int MW = mask_warps<L>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *words = reinterpret_cast<uint32_t *>(smem_raw) + warp * 256;
+    uint32_t *A = reinterpret_cast<uint32_t *>(smem_raw + (size_t)MW * 256 * 4) + warp * PT;
+    uint32_t *hit =
+        reinterpret_cast<uint32_t *>(smem_raw + (size_t)MW * (256 * 4 + PT * 4)) + warp * 32;
+    for (int j = lane; j < PT; j += 32) A[j] = 0u;
+    __syncwarp();
+    uint32_t tag = 1;
+    for (int64_t i = (int64_t)blockIdx.x * MW + warp; i < P.n; i += (int64_t)gridDim.x * MW) {
+        sample_row<L, false>(P, i, nullptr, 0, A, hit, words, tag, lane);
+        if (++tag == 0x10000u) {
+            for (int j = lane; j < PT; j += 32) A[j] = 0u;
+            __syncwarp();
+            tag = 1;
+        }
+    }
+}
+
+template <int L>
+cudaError_t launch_masks(const CompressParams &P, cudaStream_t s) {
+    const size_t smem = mask_smem_bytes<L>();
+    auto kern = mask_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, mask_warps<L>() * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (P.n + mask_warps<L>() - 1) / mask_warps<L>();
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, mask_warps<L>() * 32, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int L, bool DENSE, bool TMA, bool SPLIT = false>
 cudaError_t launch_LT(const CompressParams &P, cudaStream_t s) {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;
     constexpr int NG = kWarps / G;
     constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
-    const size_t smem = compress_smem_bytes<L, TMA>();
-    auto kern = compress_kernel<L, DENSE, TMA>;
+    const size_t smem = compress_smem_bytes<L, TMA, SPLIT>();
+    auto kern = compress_kernel<L, DENSE, TMA, SPLIT>;
     cudaError_t e0 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);
     if (e0 != cudaSuccess) return e0;
@@ -576,7 +645,14 @@ template <int L, bool DENSE>
 cudaError_t launch_L(const CompressParams &P, cudaStream_t s) {
     // bulk copies need 16-byte aligned rows whose byte length is a multiple of 16
     if constexpr (L >= 2) {
-        if (P.vec) return launch_LT<L, DENSE, true>(P, s);
+        if (P.vec) {
+            if constexpr (L > 10 && !DENSE) {
+                cudaError_t e = launch_masks<L>(P, s);
+                if (e != cudaSuccess) return e;
+                return launch_LT<L, false, true, true>(P, s);
+            }
+            return launch_LT<L, DENSE, true>(P, s);
+        }
     }
     return launch_LT<L, DENSE, false>(P, s);
 }

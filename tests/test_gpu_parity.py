@@ -72,6 +72,8 @@ def _check_compress(sk, X, m, seed, row0=0, ldx_pad=0):
     (128, 1, 77),
     (4, 4, 1),
     (700, 35, 5),
+    (3001, 150, 64),    # pt = 4096, rows not 16-byte multiples: the one-kernel path
+    (4000, 200, 129),   # pt = 4096 with padding: masks drawn by their own kernel
 ])
 def test_compress_parity(sk, p, m, n):
     X = synth.lowrank_spiky(n, p, seed=p * 7 + n, sv=(10.0, 6.0, 4.0, 2.0, 1.0)[: max(1, min(5, p))])
@@ -82,6 +84,8 @@ def test_compress_row0_and_strided(sk):
     X = synth.mixture(777, 300, 4, seed=3)[0]
     _check_compress(sk, X, 15, seed=99, row0=(1 << 33) + 17, ldx_pad=13)
     _check_compress(sk, X, 15, seed=99, row0=5, ldx_pad=4)
+    X2 = synth.mixture(150, 2500, 3, seed=5)[0]
+    _check_compress(sk, X2, 120, seed=98, row0=(1 << 33) + 3, ldx_pad=4)
 
 
 def test_compress_chunked_equals_single(sk):

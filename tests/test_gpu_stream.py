@@ -60,3 +60,44 @@ def test_streamer_rejects_device_input(sk):
     X = torch.zeros((10, 64), device="cuda")
     with pytest.raises(ValueError):
         st.run(X, None, None, None)
+
+
+def test_back_to_back_calls_do_not_race(sk):
+    """Two calls on different inputs enqueued without a host sync: the second
+    call's first copies reuse ring buffers the first call's last chunks were
+    compressed from, and must wait for them."""
+    from paper_1511_00152_gb300 import pipeline
+    mode = sk.SK_GRAM_BF16X3
+    n, p, m, seed = 40_000, 256, 16, 3
+    rng = np.random.default_rng(9)
+    X1 = torch.from_numpy(rng.standard_normal((n, p)).astype(np.float32)).pin_memory()
+    X2 = torch.from_numpy((3.0 * rng.standard_normal((n, p))).astype(np.float32)).pin_memory()
+    ctx = sk.sk_init(p, m, seed)
+    pt = ctx.pt
+    idx = torch.empty((n, m), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    Ga = torch.empty((pt, pt), dtype=torch.float64, device="cuda")
+    Gb = torch.empty_like(Ga)
+    st = pipeline.HostStreamer(ctx, 6000, mode, nbuf=2)
+    for _ in range(3):
+        st.run(X1, idx, val, Ga)
+        st.run(X2, idx, val, Gb)
+    torch.cuda.synchronize()
+
+    def one_call(Xh):
+        i1, v1 = sk.sk_compress(ctx, Xh.cuda())
+        G1 = torch.empty((pt, pt), dtype=torch.float64, device="cuda")
+        sk.sk_cov_reset(ctx, G1)
+        sk.sk_cov_accumulate(ctx, mode, i1, v1, G1)
+        torch.cuda.synchronize()
+        return i1, v1, G1
+
+    def rel(A, B):
+        A, B = torch.triu(A), torch.triu(B)
+        return float(((A - B) ** 2).sum().sqrt() / (B ** 2).sum().sqrt())
+
+    _, _, G1 = one_call(X1)
+    i2, v2, G2 = one_call(X2)
+    assert rel(Ga, G1) <= 1e-6
+    assert rel(Gb, G2) <= 1e-6
+    assert torch.equal(idx, i2) and torch.equal(val, v2)
