@@ -6,7 +6,7 @@
 // Walsh-Hadamard matrix, and the m entries of its mask are gathered into the
 // ELL output.  The transform runs on a 1024-element "unit" per warp: phase A
 // does the butterflies on element bits {0,1,7,8,9} in registers (the layout a
-// float4 load gives), a swizzled shared-memory transpose brings bits {2..6}
+// float4 load gives), a padded shared-memory transpose brings bits {2..6}
 // into registers for phase B, and for pt > 1024 a phase C across the warps of
 // a row group handles bits 10.. .  Units with pt < 1024 hold 1024/pt rows.
 //
@@ -124,10 +124,14 @@ __device__ __forceinline__ void issue_unit(const CompressParams &P, int64_t u, i
     }
 }
 
-// Swizzled shared-memory slot of unit element e: XOR of bits 2..4 with bits
-// 7..9 makes both the float4 (phase A) and the stride-4 (phase B) access
-// patterns bank-conflict free.
-__device__ __forceinline__ int phys(int e) { return e ^ (((e >> 7) & 7) << 2); }
+// Shared-memory slot of unit element e: four floats of padding after every
+// 128 elements.  The float4 rows of phase A (e = 128 ip + 4 lane) and the
+// stride-4 columns of phase B (e = 128 ib + 4 j + q, bank 4 ib + q + 4 j) are
+// then bank-conflict free, and each access is a per-lane base plus a
+// compile-time offset (no per-access address arithmetic).  A 1024-element
+// unit segment takes kSeg floats.
+constexpr int kSeg = 1024 + 32;
+__device__ __forceinline__ int phys(int e) { return e + ((e >> 7) << 2); }
 
 template <int G>
 __device__ __forceinline__ void group_sync(int grp) {
@@ -143,7 +147,7 @@ __device__ __forceinline__ int yaddr(int ebase, int c) {
     if constexpr (L <= 10) {
         return phys(ebase + c);
     } else {
-        return ((c >> 10) << 10) + phys(c & 1023);
+        return (c >> 10) * kSeg + phys(c & 1023);
     }
 }
 
@@ -288,7 +292,7 @@ constexpr size_t compress_smem_bytes() {
     constexpr int PT = 1 << L;
     constexpr int G = (L > 10) ? (PT >> 10) : 1;
     constexpr int NG = kWarps / G;
-    constexpr int BUF = (L <= 10) ? 1024 : PT;
+    constexpr int BUF = (L <= 10) ? kSeg : (PT >> 10) * kSeg;
     constexpr int NBUF = TMA ? kNB : 1;
     constexpr int NA = SPLIT ? 0 : PT;  // the mask kernel holds the Fisher-Yates arrays
     return kFixedSmem + (size_t)NG * NBUF * BUF * 4 + (size_t)NG * NA * 4 + (size_t)NG * 32 * 4;
@@ -319,7 +323,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
     constexpr int G = (L > 10) ? (PT >> 10) : 1;  // warps per row group
     constexpr int NG = kWarps / G;                // row groups per CTA
     constexpr int RPU = (L <= 10) ? (1024 >> L) : 1;
-    constexpr int BUF = (L <= 10) ? 1024 : PT;
+    constexpr int BUF = (L <= 10) ? kSeg : (PT >> 10) * kSeg;
     constexpr int NBUF = TMA ? kNB : 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = warp / G, wg = warp % G;
@@ -357,7 +361,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
         group_sync<G>(grp);
         if (u_first < nunits) {
             const int b0 = (int)(kloc & 1);
-            issue_unit<L>(P, u_first, wg, ybufs + b0 * BUF + ((L > 10) ? 1024 * wg : 0),
+            issue_unit<L>(P, u_first, wg, ybufs + b0 * BUF + ((L > 10) ? kSeg * wg : 0),
                           smem_u32(mbar + b0), lane);
         }
     }
@@ -371,7 +375,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             group_sync<G>(grp);
             if (u + stride < nunits)
-                issue_unit<L>(P, u + stride, wg, ybufs + (bsel ^ 1) * BUF + ((L > 10) ? 1024 * wg : 0),
+                issue_unit<L>(P, u + stride, wg, ybufs + (bsel ^ 1) * BUF + ((L > 10) ? kSeg * wg : 0),
                               smem_u32(mbar + (bsel ^ 1)), lane);
             if (!mbar_wait_bounded(smem_u32(mbar + bsel), (uint32_t)((kloc >> 1) & 1))) {
                 if (lane == 0 && P.err) atomicOr(P.err, 2u);
@@ -381,7 +385,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
                 ok = false;
                 break;
             }
-            float *wb = ybuf + ((L > 10) ? 1024 * wg : 0);
+            float *wb = ybuf + ((L > 10) ? kSeg * wg : 0);
             // zero what the copies did not fill: padding columns and rows past n
             const bool ragged = (L <= 10) ? (r0 + RPU > P.n) : false;
             const int cend = (L <= 10) ? (int)P.p : (int)(P.p - 1024 * wg);
@@ -455,7 +459,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
         }
         // every lane has read its samples (TMA) / previous gathers are done
         group_sync<G>(grp);
-        float *wbuf = ybuf + ((L > 10) ? 1024 * wg : 0);
+        float *wbuf = ybuf + ((L > 10) ? kSeg * wg : 0);
 #pragma unroll
         for (int ip = 0; ip < 8; ++ip) {
             const int e = 128 * ip + 4 * lane;
@@ -488,16 +492,16 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
             for (int s2 = 0; s2 < S; ++s2)
 #pragma unroll
                 for (int w3 = 0; w3 < G; w3 += 2)
-                    w2[(s2 * G + w3) >> 1] = pk2(ybuf[1024 * w3 + phys(tau + 32 * G * s2)],
-                                                 ybuf[1024 * (w3 + 1) + phys(tau + 32 * G * s2)]);
+                    w2[(s2 * G + w3) >> 1] = pk2(ybuf[kSeg * w3 + phys(tau + 32 * G * s2)],
+                                                 ybuf[kSeg * (w3 + 1) + phys(tau + 32 * G * s2)]);
 #pragma unroll
             for (int rb = 0; (1 << rb) < G; ++rb) wht_stage<16>(w2, rb);
 #pragma unroll
             for (int s2 = 0; s2 < S; ++s2)
 #pragma unroll
                 for (int w3 = 0; w3 < G; w3 += 2) {
-                    ybuf[1024 * w3 + phys(tau + 32 * G * s2)] = lo2(w2[(s2 * G + w3) >> 1]);
-                    ybuf[1024 * (w3 + 1) + phys(tau + 32 * G * s2)] = hi2(w2[(s2 * G + w3) >> 1]);
+                    ybuf[kSeg * w3 + phys(tau + 32 * G * s2)] = lo2(w2[(s2 * G + w3) >> 1]);
+                    ybuf[kSeg * (w3 + 1) + phys(tau + 32 * G * s2)] = hi2(w2[(s2 * G + w3) >> 1]);
                 }
         }
         group_sync<G>(grp);
