@@ -67,6 +67,8 @@ def load(path: str | None = None):
             "sk_kmeans_update": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp]),
             "sk_kmeans_step": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),
             "sk_kmeans_step_delta": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+            "sk_kmeans_step_auto": (st, [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp, i32,
+                                         vp]),
             "sk_kmeans_finalize": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_unmix": (st, [vp, vp, i64, vp, vp]),
             "sk_unmix_f64": (st, [vp, vp, i64, vp, vp]),
@@ -321,6 +323,17 @@ def sk_kmeans_step_delta(ctx: Ctx, idx, val, mu, labels, S, cnt, nk, dist=None, 
     _check("sk_kmeans_step_delta", load().sk_kmeans_step_delta(
         ctx.handle, _ptr(idx), _ptr(val), n, _ptr(mu), K, _ptr(labels), _ptr(dist), _ptr(S),
         _ptr(cnt), _ptr(nk), _ptr(changed), _stream(stream)))
+    return labels
+
+
+def sk_kmeans_step_auto(ctx: Ctx, idx, val, mu, labels, S, cnt, nk, state, first: bool,
+                        dist=None, stream=None):
+    n = idx.shape[0]
+    K = mu.shape[0]
+    _need(state, torch.int64, "state", (2,))
+    _check("sk_kmeans_step_auto", load().sk_kmeans_step_auto(
+        ctx.handle, _ptr(idx), _ptr(val), n, _ptr(mu), K, _ptr(labels), _ptr(dist), _ptr(S),
+        _ptr(cnt), _ptr(nk), _ptr(state), 1 if first else 0, _stream(stream)))
     return labels
 
 

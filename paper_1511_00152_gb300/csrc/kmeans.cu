@@ -53,6 +53,11 @@ struct KmParams {
     unsigned long long *changed;  // delta mode: rows whose label changed (may be NULL)
     int do_assign;
     int do_update;  // 0 none, 1 full sums, 2 incremental (changed rows only)
+    // adaptive passes: the kernel runs only if *mode == expect (mode NULL:
+    // always); a full pass with changed != NULL counts the rows whose label
+    // differs from the one labels held before the pass
+    const int64_t *mode;
+    int expect;
 };
 
 // Packed FP32 pairs (two independent IEEE round-to-nearest operations).
@@ -125,7 +130,7 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
         // previous label (incremental mode), loaded before the distance loop so
         // the load latency overlaps it
         int old_pref = -1;
-        if (P.do_update == 2 && row_ok && kl == 0) old_pref = P.labels[i];
+        if ((P.do_update == 2 || P.changed) && row_ok && kl == 0) old_pref = P.labels[i];
         if (P.do_assign) {
             uint64_t acc[NP];
 #pragma unroll
@@ -199,6 +204,10 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
             if (row_ok && kl == 0) {
                 P.labels[i] = label;
                 if (P.dist) P.dist[i] = bd;
+            }
+            if (P.do_update != 2 && P.changed) {
+                const unsigned mv = __ballot_sync(kFull, row_ok && kl == 0 && old != label);
+                if (lane == 0 && mv) atomicAdd(P.changed, (unsigned long long)__popc(mv));
             }
             if (P.do_update == 2) {
                 // incremental sums: a row whose label moved from old to label
@@ -303,6 +312,7 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
 template <int KPL, bool MU_SMEM, bool PRIV, bool STAGE, bool COPIES>
 __global__ void __launch_bounds__(kThreads) kmeans_kernel(KmParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (P.mode && *P.mode != P.expect) return;  // the other kind of pass runs
     size_t off = 0;
     float *mus = reinterpret_cast<float *>(smem_raw + off);
     if (MU_SMEM && P.do_assign) off += (size_t)P.pt * (COPIES ? 32 : P.Kpad) * 4;
@@ -365,6 +375,30 @@ __global__ void kmeans_finalize_kernel(int64_t KP, const double *S, const int32_
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = cnt[e];
         if (c > 0) mu[e] = (float)(S[e] / (double)c);
+    }
+}
+
+// Adaptive pass, first step (one CTA): state[0] holds the number of rows
+// whose label changed in the previous pass.  If that is more than thr (or
+// this is the first pass), this pass rebuilds the sums from zero: the sums
+// are zeroed here and state[1] = 1 selects the full pass; otherwise
+// state[1] = 2 selects the incremental pass.  state[0] restarts at 0 and the
+// pass that runs adds its own count of changed rows to it.
+__global__ void kmeans_auto_decide_kernel(int64_t *state, int64_t thr, int first, int64_t KP,
+                                          int K, double *S, int32_t *cnt, int64_t *nk) {
+    __shared__ int full;
+    if (threadIdx.x == 0) full = (first || state[0] > thr) ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        state[1] = full ? 1 : 2;
+        state[0] = 0;
+    }
+    if (full) {
+        for (int64_t e = threadIdx.x; e < KP; e += blockDim.x) {
+            S[e] = 0.0;
+            cnt[e] = 0;
+        }
+        for (int e = threadIdx.x; e < K; e += blockDim.x) nk[e] = 0;
     }
 }
 
@@ -541,10 +575,41 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
 
 }  // namespace
 
+static cudaError_t launch_kmeans_mode(const sk_ctx &c, const int32_t *idx, const float *val,
+                                      int64_t n, const float *mu, int K, int32_t *labels,
+                                      float *dist, double *S, int32_t *cnt, int64_t *nk,
+                                      bool do_assign, int do_update, int64_t *changed,
+                                      const int64_t *mode, int expect, cudaStream_t s);
+
 cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
                           int64_t n, const float *mu, int K, int32_t *labels, float *dist,
                           double *S, int32_t *cnt, int64_t *nk, bool do_assign,
                           int do_update, int64_t *changed, cudaStream_t s) {
+    return launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, do_assign,
+                              do_update, changed, nullptr, 0, s);
+}
+
+cudaError_t launch_kmeans_auto(const sk_ctx &c, const int32_t *idx, const float *val,
+                               int64_t n, const float *mu, int K, int32_t *labels, float *dist,
+                               double *S, int32_t *cnt, int64_t *nk, int64_t *state, int first,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    kmeans_auto_decide_kernel<<<1, 1024, 0, s>>>(state, n / 16, first, (int64_t)K * c.pt, K, S,
+                                                 cnt, nk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, true, 1, state,
+                           state + 1, 1, s);
+    if (e != cudaSuccess) return e;
+    return launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, true, 2, state,
+                              state + 1, 2, s);
+}
+
+static cudaError_t launch_kmeans_mode(const sk_ctx &c, const int32_t *idx, const float *val,
+                                      int64_t n, const float *mu, int K, int32_t *labels,
+                                      float *dist, double *S, int32_t *cnt, int64_t *nk,
+                                      bool do_assign, int do_update, int64_t *changed,
+                                      const int64_t *mode, int expect, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     KmParams P;
     P.idx = idx;
@@ -562,6 +627,8 @@ cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
     P.do_assign = do_assign;
     P.do_update = do_update;
     P.changed = reinterpret_cast<unsigned long long *>(changed);
+    P.mode = mode;
+    P.expect = expect;
     if (K <= 64) return launch_kpl<2>(P, s);
     if (K <= 128) return launch_kpl<4>(P, s);
     return launch_kpl<8>(P, s);

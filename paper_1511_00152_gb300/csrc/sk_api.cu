@@ -272,6 +272,20 @@ sk_status sk_kmeans_step_delta(const sk_ctx *ctx, const int32_t *idx, const floa
                        "sk_kmeans_step_delta");
 }
 
+sk_status sk_kmeans_step_auto(const sk_ctx *ctx, const int32_t *idx, const float *val,
+                              int64_t n, const float *mu, int32_t K, int32_t *labels, float *dist,
+                              double *S, int32_t *cnt, int64_t *nk, int64_t *state, int32_t first,
+                              void *stream) {
+    sk_status st = kmeans_common("sk_kmeans_step_auto", ctx, idx, val, n, K);
+    if (st != SK_OK) return st;
+    if (n == 0) return SK_OK;
+    if (!mu || !labels || !S || !cnt || !nk || !state)
+        return fail(SK_EINVAL, "sk_kmeans_step_auto: NULL buffer");
+    return cuda_status(sk::launch_kmeans_auto(*ctx, idx, val, n, mu, K, labels, dist, S, cnt, nk,
+                                              state, first ? 1 : 0, as_stream(stream)),
+                       "sk_kmeans_step_auto");
+}
+
 sk_status sk_kmeans_finalize(const sk_ctx *ctx, int32_t K, const double *S, const int32_t *cnt,
                              float *mu, void *stream) {
     SK_CHECK_CTX(ctx);

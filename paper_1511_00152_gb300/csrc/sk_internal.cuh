@@ -184,6 +184,12 @@ cudaError_t launch_kmeans(const sk_ctx &c, const int32_t *idx, const float *val,
                           int64_t n, const float *mu, int K, int32_t *labels, float *dist,
                           double *S, int32_t *cnt, int64_t *nk, bool do_assign,
                           int do_update, int64_t *changed, cudaStream_t s);
+// Adaptive pass (sk_kmeans_step_auto): full or incremental sums, chosen on
+// the device from state[0], the previous pass's count of changed labels.
+cudaError_t launch_kmeans_auto(const sk_ctx &c, const int32_t *idx, const float *val,
+                               int64_t n, const float *mu, int K, int32_t *labels, float *dist,
+                               double *S, int32_t *cnt, int64_t *nk, int64_t *state, int first,
+                               cudaStream_t s);
 cudaError_t launch_kmeans_finalize(const sk_ctx &c, int K, const double *S,
                                    const int32_t *cnt, float *mu, cudaStream_t s);
 cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *val,

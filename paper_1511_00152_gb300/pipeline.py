@@ -13,7 +13,8 @@ from . import _lib as sk
 class KMeansState:
     """Device buffers of one sparsified K-means run (Algorithm 1 loop)."""
 
-    def __init__(self, ctx: sk.Ctx, n: int, K: int, device="cuda", keep_dist: bool = False):
+    def __init__(self, ctx: sk.Ctx, n: int, K: int, device="cuda", keep_dist: bool = False,
+                 mode: str = "auto"):
         self.ctx, self.n, self.K = ctx, n, K
         self.mu = torch.empty((K, ctx.pt), dtype=torch.float32, device=device)
         self.labels = torch.empty(n, dtype=torch.int32, device=device)
@@ -23,17 +24,24 @@ class KMeansState:
         self.cnt = torch.empty((K, ctx.pt), dtype=torch.int32, device=device)
         self.nk = torch.empty(K, dtype=torch.int64, device=device)
         self.changed = torch.zeros(1, dtype=torch.int64, device=device)
-        self.incremental = True
+        # how passes after the first update the sums: "auto" (full rebuild
+        # while many labels change, incremental after; chosen on the device),
+        # "incremental" or "full"
+        self.mode = mode
+        self.state = torch.zeros(2, dtype=torch.int64, device=device)
         self.graph = None
         self._graph_args = None
 
     def iteration(self, idx, val, first: bool = True, stream=None):
         """One assign + update pass (Eqs. (assignments), (mu_update_two)).
 
-        The first pass builds the sums from scratch; later passes update them
-        incrementally from the rows whose label changed (same sums)."""
+        The first pass builds the sums from scratch; later passes rebuild them
+        or update them from the rows whose label changed (same sums)."""
         ctx = self.ctx
-        if first or not self.incremental:
+        if self.mode == "auto":
+            sk.sk_kmeans_step_auto(ctx, idx, val, self.mu, self.labels, self.S, self.cnt, self.nk,
+                                   self.state, first, dist=self.dist, stream=stream)
+        elif first or self.mode == "full":
             sk.sk_kmeans_reset(ctx, self.S, self.cnt, self.nk, stream=stream)
             sk.sk_kmeans_step(ctx, idx, val, self.mu, self.labels, self.S, self.cnt, self.nk,
                               dist=self.dist, stream=stream)

@@ -349,10 +349,9 @@ def test_kmeans_incremental_sums_match_recomputed(sk, p, m, n, K):
     idx, val = _dev(oi), _dev(v32)
     rows = synth.init_rows(n, K, seed)
     mu0 = pipeline.initial_centres(ctx, Xd, rows)
-    a = pipeline.KMeansState(ctx, n, K)
+    a = pipeline.KMeansState(ctx, n, K, mode="incremental")
     la, mua = a.run(idx, val, mu0, iters=8, use_graph=False)
-    b = pipeline.KMeansState(ctx, n, K)
-    b.incremental = False
+    b = pipeline.KMeansState(ctx, n, K, mode="full")
     lb, mub = b.run(idx, val, mu0, iters=8, use_graph=False)
     torch.cuda.synchronize()
     agree = float((la == lb).float().mean())
@@ -373,3 +372,51 @@ def test_kmeans_incremental_sums_match_recomputed(sk, p, m, n, K):
     # the first pass sums per-CTA float partials, later passes add FP64 deltas
     assert np.abs(a.S.cpu().numpy() - So).max() <= 1e-5 * (np.abs(So).max() + 1e-30)
     assert int(a.changed.item()) > 0
+
+
+@pytest.mark.parametrize("p,m,n,K", [(64, 8, 2000, 5), (1024, 51, 20000, 10), (256, 5, 5000, 50)])
+def test_kmeans_auto_pass_matches_full(sk, p, m, n, K):
+    """sk_kmeans_step_auto (full rebuild while many labels change, then
+    incremental, chosen on the device) runs the same iteration as full
+    rebuilds every pass: the same labels, and sums that describe the final
+    labels exactly (counts) or to FP64 rounding (S), eagerly and in a graph."""
+    from paper_1511_00152_gb300 import pipeline
+    X = synth.mixture(n, p, min(K, 10), seed=p + n + 1)[0]
+    seed = 31
+    ctx = sk.sk_init(p, m, seed)
+    Xd = _dev(X)
+    oi, ov = oracle.compress(X, m, seed)
+    v32 = ov.astype(np.float32)
+    idx, val = _dev(oi), _dev(v32)
+    rows = synth.init_rows(n, K, seed)
+    mu0 = pipeline.initial_centres(ctx, Xd, rows)
+    a = pipeline.KMeansState(ctx, n, K, mode="auto")
+    a.mu.copy_(mu0)
+    modes = []
+    for it in range(8):
+        a.iteration(idx, val, first=(it == 0))
+        modes.append(int(a.state[1].item()))
+    b = pipeline.KMeansState(ctx, n, K, mode="full")
+    lb, mub = b.run(idx, val, mu0, iters=8, use_graph=False)
+    g = pipeline.KMeansState(ctx, n, K, mode="auto")
+    lg, mug = g.run(idx, val, mu0, iters=8, use_graph=True)
+    torch.cuda.synchronize()
+    assert modes[0] == 1  # the first pass always rebuilds
+    assert set(modes) <= {1, 2}
+    for la, mua in ((a.labels, a.mu), (lg, mug)):
+        agree = float((la == lb).float().mean())
+        assert agree >= 0.999, agree
+        if agree == 1.0:
+            assert torch.allclose(mua, mub, rtol=1e-5, atol=1e-6)
+    labs = a.labels.cpu().numpy().astype(np.int64)
+    lk = np.repeat(labs, m)
+    counts_o = np.zeros((K, ctx.pt), np.int64)
+    So = np.zeros((K, ctx.pt))
+    np.add.at(counts_o, (lk, oi.ravel()), 1)
+    np.add.at(So, (lk, oi.ravel()), v32.astype(np.float64).ravel())
+    assert np.array_equal(a.cnt.cpu().numpy(), counts_o)
+    assert np.array_equal(a.nk.cpu().numpy(), np.bincount(labs, minlength=K))
+    assert np.abs(a.S.cpu().numpy() - So).max() <= 1e-5 * (np.abs(So).max() + 1e-30)
+    # state[0] is the last pass's count of changed rows
+    assert 0 <= int(a.state[0].item()) <= n
+    assert sk.sk_device_status() == sk.SK_OK
