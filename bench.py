@@ -47,10 +47,10 @@ UNIT = "samples/s"
 # dominant kernel from one ncu capture of this workload (profiles/), valid only
 # while the kernel source still has the digest it had when captured.
 KERNEL_TRAFFIC = {
-    # profiles/kmeans_kernel_n4e5_p1024_K10.md: 164.92 MB read + 3.92 MB written
-    # per incremental pass at n = 400,000 (422.1 B per row), scaled to n = 10^6
-    "kmeans": {"bytes": 422_120_000, "n": 1_000_000, "p": 1024,
-               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "35716e1e0ad182e9"},
+    # profiles/kmeans_kernel_n4e5_p1024_K10.md: 164.88 MB read + 3.92 MB written
+    # per incremental pass at n = 400,000 (422.0 B per row), scaled to n = 10^6
+    "kmeans": {"bytes": 422_000_000, "n": 1_000_000, "p": 1024,
+               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "7710672b8470aee7"},
 }
 
 
@@ -138,6 +138,46 @@ def dist_setup(args):
         dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
+
+
+def gpu_local_cpus(index: int):
+    """CPUs on the GPU's own NUMA node: the PCI device's local_cpulist in sysfs,
+    else the CPU affinity `nvidia-smi topo -m` prints; None if neither says."""
+    import torch
+
+    def parse(text):
+        cpus = set()
+        for part in text.strip().split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part.strip():
+                cpus.add(int(part))
+        return cpus or None
+
+    try:
+        pr = torch.cuda.get_device_properties(index)
+        bus = "%04x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), pr.pci_bus_id,
+                                    pr.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as fh:
+            cpus = parse(fh.read())
+        if cpus and len(cpus) < (os.cpu_count() or 0):
+            return cpus
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True,
+                             timeout=20).stdout.splitlines()
+        head = next(line for line in out if "CPU Affinity" in line)
+        col = head.split("\t").index("CPU Affinity") if "\t" in head else None
+        row = next(line for line in out if line.startswith(f"GPU{index}"))
+        fields = row.split("\t") if col is not None else row.split()
+        cpus = parse(fields[col] if col is not None else fields[-2])
+        if cpus and len(cpus) < (os.cpu_count() or 0):
+            return cpus
+    except Exception:
+        pass
+    return None
 
 
 def max_over_ranks(value: float, pg, device=None) -> float:
@@ -383,6 +423,11 @@ def run_gpu(args, cfg):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
+        # pinned host buffers on the GPU's own NUMA node (first touch by a
+        # thread on a local CPU), so the host link is not crossed twice
+        host_cpus = gpu_local_cpus(local)
+        if host_cpus:
+            os.sched_setaffinity(0, host_cpus)
         Xh = torch.empty((n, p), dtype=torch.float32, pin_memory=True)
         Xh.copy_(X)
         # the seeded start rows, picked on the host (input preparation)
@@ -429,7 +474,9 @@ def run_gpu(args, cfg):
         e2e = {"value": world * n / (ems * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": n * p * 4 + K * p * 4,
                "d2h_bytes_per_step": n * 4 + K * p * 4 + k * p * 8,
-               "ms_per_step": ems}
+               "ms_per_step": ems,
+               "host_cpus": (f"{min(host_cpus)}-{max(host_cpus)} ({len(host_cpus)}, GPU-local)"
+                             if host_cpus else "any")}
         del Xh
 
     # the plain FP32 GPU form of the covariance pass (shared-memory scatter
