@@ -201,7 +201,8 @@ def barrier(pg, device=None):
 # ------------------------------------------------------------------ CPU oracle
 
 def oracle_step(X, cfg, rows_init):
-    """One step of the oracle on a row sample (compress, C_n, top-k, K-means)."""
+    """One step of the oracle on a row sample (compress, C_n, top-k, K-means);
+    returns its results for the accuracy comparison."""
     import oracle
     n, p = X.shape
     m, K = cfg["m"], cfg["K"]
@@ -214,7 +215,7 @@ def oracle_step(X, cfg, rows_init):
     mu0 = oracle.precondition(X[rows_init], seed)
     labels, mu, _ = oracle.kmeans(idx, val, mu0, pt, cfg["iters"])
     oracle.unmix(mu, p, seed)
-    return labels
+    return {"idx": idx, "val": val, "C": C, "evals": w, "V": V, "labels": labels, "mu": mu}
 
 
 def cpu_sample(cfg, rows: int):
@@ -228,9 +229,58 @@ def time_cpu_baseline(cfg, rows=4000):
     X, ri = cpu_sample(cfg, rows)
     oracle_step(X[:200], cfg, synth_rows(200, cfg))  # compile/warm the oracle
     t = time.perf_counter()
-    oracle_step(X, cfg, ri)
+    ref = oracle_step(X, cfg, ri)
     dt = time.perf_counter() - t
-    return rows / dt, dt
+    return rows / dt, dt, (X, ri, ref)
+
+
+def accuracy_vs_oracle(sk, pipeline, ctx, mode, topk_iters, gwork, work, sample, cfg, dev):
+    """The GPU path on the oracle's row sample (untimed), each result against
+    the FP64 oracle's: idx exact, val relative to the row norm, C_n relative
+    Frobenius, top-k eigenvalues and principal angles, centres and labels
+    after the K-means iterations."""
+    import numpy as np
+    import torch
+    X, ri, ref = sample
+    rows, p = X.shape
+    m, K, k, iters = cfg["m"], cfg["K"], cfg["pca_k"], cfg["iters"]
+    pt = ctx.pt
+    Xd = torch.as_tensor(X, device=dev)
+    idx, val = sk.sk_compress(ctx, Xd)
+    G = torch.empty((pt, pt), dtype=torch.float64, device=dev)
+    sk.sk_cov_reset(ctx, G)
+    sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=gwork)
+    C = torch.empty_like(G)
+    sk.sk_cov_finalize(ctx, G, rows, C=C)
+    ev = torch.empty(k, dtype=torch.float64, device=dev)
+    U = torch.empty((k, pt), dtype=torch.float64, device=dev)
+    sk.sk_cov_topk(ctx, C, k, topk_iters, evals=ev, U=U, work=work)
+    mu0 = sk.sk_precondition(ctx, Xd[torch.as_tensor(ri, device=dev)].contiguous())
+    st = pipeline.KMeansState(ctx, rows, K, device=dev)
+    labels, mu = st.run(idx, val, mu0, iters, use_graph=False)
+    torch.cuda.synchronize()
+    idx_h, val_h = idx.cpu().numpy(), val.cpu().numpy().astype(np.float64)
+    norms = np.linalg.norm(X.astype(np.float64), axis=1)
+    Co, Cg = ref["C"], C.cpu().numpy()
+    Vo, Vg = ref["V"], U.cpu().numpy().T
+    Qg, _ = np.linalg.qr(Vg)
+    # largest principal angle: sin = ||(I - Vo Vo^T) Qg||_2 (accurate for small angles)
+    sin_max = float(np.linalg.norm(Qg - Vo @ (Vo.T @ Qg), 2))
+    evo, evg = ref["evals"], ev.cpu().numpy()
+    muo, mug = ref["mu"], mu.cpu().numpy().astype(np.float64)
+    return {
+        "rows": rows, "against": "FP64 oracle on the same rows",
+        "idx_rows_exact": float(np.mean(np.all(idx_h == ref["idx"], axis=1))),
+        "val_max_err_rel_row_norm": float(np.max(np.abs(val_h - ref["val"]).max(axis=1) / norms)),
+        "cov_rel_frobenius": float(np.linalg.norm(Cg - Co) / np.linalg.norm(Co)),
+        "topk_eigenvalue_max_rel_err": float(np.max(np.abs(evg - evo) / np.abs(evo))),
+        "topk_max_sin_principal_angle": sin_max,
+        "kmeans_label_agreement": float(np.mean(labels.cpu().numpy() == ref["labels"])),
+        "kmeans_centre_rel_err": float(np.linalg.norm(mug - muo) / np.linalg.norm(muo)),
+        "notes": (f"Gram mode {cfg.get('gram', '')}; top-{k} by {topk_iters} subspace iterations "
+                  f"(oracle: LAPACK eigh); {iters} K-means iterations end to end (a flipped "
+                  "near-tie can move a trajectory, so the label figure is an agreement)"),
+    }
 
 
 def synth_rows(n, cfg):
@@ -500,13 +550,21 @@ def run_gpu(args, cfg):
                  "step_value": world * n / ((ms - stage_ms["gram"] + g32) * 1e-3)}
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu:
         try:
-            v, dt = time_cpu_baseline(cfg, rows=args.cpu_rows)
+            v, dt, sample = time_cpu_baseline(cfg, rows=args.cpu_rows)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{args.cpu_rows} rows of the workload (full p, m, K, iters), {dt:.1f} s"}
         except Exception as exc:  # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+            sample = None
+        if sample is not None:
+            try:
+                accuracy = accuracy_vs_oracle(sk, pipeline, ctx, mode, args.topk_iters, gwork, work,
+                                              sample, dict(cfg, gram=args.gram), dev)
+            except Exception as exc:  # report, do not hide
+                accuracy = {"failed": repr(exc)}
 
     if rank == 0:
         line = {
@@ -522,7 +580,7 @@ def run_gpu(args, cfg):
             "stage_ms": stage_ms, "kmeans_iter_ms": kmeans_iter_ms,
             "pca_max_rel_residual": pca_res,
             "roofline": roof, "stage_rooflines": roofs, "plain_fp32_form": plain,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "cpu_baseline": cpu, "accuracy_vs_fp64": accuracy, "e2e": e2e, "clocks": clocks,
             "gpu_launches": sum(launches.values()) * args.steps,
         }
         print(json.dumps(line), flush=True)

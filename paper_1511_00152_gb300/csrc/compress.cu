@@ -233,18 +233,42 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
         uint64_t prod = 0;
         uint32_t wtop = (uint32_t)c0 + woff + 31;
         ensure_batches(ww, P, g, (uint32_t)c0 + woff, wtop, lane);
-        for (;;) {
-            const uint32_t word = act ? words[((w >> 7) & 1) * 128 + (w & 127)] : 0u;
+        if constexpr (GATHER) {
+            for (;;) {
+                const uint32_t word = act ? words[((w >> 7) & 1) * 128 + (w & 127)] : 0u;
+                prod = (uint64_t)word * (uint64_t)s;
+                bool rej = false;
+                if (act && (uint32_t)prod < s) rej = (uint32_t)prod < ((0u - s) % s);
+                const unsigned bal = __ballot_sync(kFull, rej);
+                if (bal == 0u) break;
+                const int first = __ffs(bal) - 1;
+                if (lane >= first) ++w;
+                ++woff;
+                ++wtop;
+                ensure_batches(ww, P, g, (uint32_t)c0 + woff, wtop, lane);
+            }
+        } else {
+            // masks alone (mask_kernel): a rejection needs (L mod 2^32) < s
+            // first, probability below s / 2^32; only if some lane meets it
+            // is the exact threshold 2^32 mod s taken (same draws; measured
+            // faster in this kernel, slower inside the fused one)
+            uint32_t word = act ? words[((w >> 7) & 1) * 128 + (w & 127)] : 0u;
             prod = (uint64_t)word * (uint64_t)s;
-            bool rej = false;
-            if (act && (uint32_t)prod < s) rej = (uint32_t)prod < ((0u - s) % s);
-            const unsigned bal = __ballot_sync(kFull, rej);
-            if (bal == 0u) break;
-            const int first = __ffs(bal) - 1;
-            if (lane >= first) ++w;
-            ++woff;
-            ++wtop;
-            ensure_batches(ww, P, g, (uint32_t)c0 + woff, wtop, lane);
+            if (__any_sync(kFull, act && (uint32_t)prod < s)) {
+                for (;;) {
+                    bool rej = false;
+                    if (act && (uint32_t)prod < s) rej = (uint32_t)prod < ((0u - s) % s);
+                    const unsigned bal = __ballot_sync(kFull, rej);
+                    if (bal == 0u) break;
+                    const int first = __ffs(bal) - 1;
+                    if (lane >= first) ++w;
+                    ++woff;
+                    ++wtop;
+                    ensure_batches(ww, P, g, (uint32_t)c0 + woff, wtop, lane);
+                    word = act ? words[((w >> 7) & 1) * 128 + (w & 127)] : 0u;
+                    prod = (uint64_t)word * (uint64_t)s;
+                }
+            }
         }
         const int k = act ? t + (int)(prod >> 32) : -1 - lane;
         const unsigned grpm = __match_any_sync(kFull, k);
@@ -256,7 +280,9 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
         __syncwarp();
         const unsigned srcm = act ? (hit[lane] & lt) : 0u;
         const int src = srcm ? 31 - __clz(srcm) : lane;
-        const int vbase = act ? readA(A, tag, t) : 0;
+        // a row's first chunk finds every position still holding its own
+        // index (the mask kernel skips that look-up)
+        const int vbase = act ? ((GATHER || c0) ? readA(A, tag, t) : t) : 0;
         int V = vbase;  // value at position t just before step t
         for (;;) {
             const int from = __shfl_sync(kFull, V, src);
@@ -269,7 +295,7 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
         const int prev = prevm ? 31 - __clz(prevm) : lane;
         const int vprev = __shfl_sync(kFull, V, prev);
         int omega = 0;
-        if (act) omega = prevm ? vprev : readA(A, tag, k);
+        if (act) omega = prevm ? vprev : ((GATHER || c0) ? readA(A, tag, k) : k);
         __syncwarp();
         if (act && c0 + 32 < m && (grpm & gt) == 0u && k >= c0 + 32)
             A[k] = (tag << 16) | (uint32_t)V;
