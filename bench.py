@@ -548,6 +548,33 @@ def run_gpu(args, cfg):
         plain = {"gram": "fp32", "gram_ms": g32, "chosen_gram_ms": stage_ms["gram"],
                  "speedup": g32 / stage_ms["gram"],
                  "step_value": world * n / ((ms - stage_ms["gram"] + g32) * 1e-3)}
+    # the unfused form of the compress pass: the dense y = HDx written to HBM
+    # (sk_precondition), then its entries at the same mask stream gathered by
+    # sk_compress of a context without preconditioning (pt columns)
+    if not args.no_plain and p == pt:
+        ctx_raw = sk.sk_init_ex(pt, m, seed, sk.SK_FLAG_NO_PRECONDITION)
+        Yd = torch.empty((n, pt), dtype=torch.float32, device=dev)
+        idx2 = torch.empty_like(idx)
+        val2 = torch.empty_like(val)
+        sk.sk_precondition(ctx, X, Y=Yd)
+        sk.sk_compress(ctx_raw, Yd, idx=idx2, val=val2)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            sk.sk_precondition(ctx, X, Y=Yd)
+            sk.sk_compress(ctx_raw, Yd, idx=idx2, val=val2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tu = a.elapsed_time(b) / 3
+        unfused = {"form": "sk_precondition (dense y to HBM) + sk_compress of y, no preconditioning",
+                   "compress_ms": tu, "fused_compress_ms": stage_ms["compress"],
+                   "speedup": tu / stage_ms["compress"],
+                   "bytes_per_row": 3 * 4 * pt + 8 * m,
+                   "same_output": bool(torch.equal(idx2, idx) and torch.equal(val2, val))}
+        plain = dict(plain or {}, compress_unfused=unfused)
+        del Yd, idx2, val2
 
     cpu = None
     accuracy = None
