@@ -1,4 +1,4 @@
-"""Pins from the paper's theorems on the oracle's preconditioner and sample mean.
+"""Pins from the paper's theorems on the oracle's preconditioner and estimators.
 
 * Sec. IV, proof of the sample-mean theorem: the per-sample error covariance
   Lambda = E[(p/m R R^T x - x)(p/m R R^T x - x)^T] has the closed form
@@ -11,6 +11,8 @@
   single spike to a flat vector of entries +-1/sqrt(p).
 * Appendix D, the pairwise-distance theorem: ||sqrt(p/m) R^T H D (x1 - x2)||
   lies in [0.40, 1.48] ||x1 - x2|| with high probability.
+* Sec. V, the covariance theorem: ||C_n - C_emp||_2 <= t(delta_2) from its
+  matrix Bernstein bound, on the model of the paper's own experiment.
 """
 import itertools
 
@@ -123,3 +125,49 @@ def test_pairwise_distance_ratio_in_band():
         rr = np.sqrt(p / m) * np.linalg.norm(raw) / nd
         out_raw += not (0.40 <= rr <= 1.48)
     assert out_raw >= 90  # nearly every one-spike difference, without preconditioning
+
+
+def _cov_bound(X64, m, rho, delta):
+    """t with P{||C_n - C_emp||_2 <= t} >= 1 - delta from the covariance
+    theorem of Sec. V (L and the bound on sigma^2 as stated there, the matrix
+    Bernstein tail solved for t); X64 holds the samples as rows."""
+    n, p = X64.shape
+    Cemp = X64.T @ X64 / n
+    maxcol2 = (X64 ** 2).sum(axis=1).max()  # ||X||_maxCol^2: largest sample norm
+    xmax2 = np.abs(X64).max() ** 2
+    fro2 = (X64 ** 2).sum()
+    x4 = (X64 ** 4).sum(axis=0).max()
+    a = p * (p - 1) / (m * (m - 1))
+    L = ((a * rho + 1) * maxcol2 + p * (p - m) / (m * (m - 1)) * xmax2) / n
+    s2 = ((a * rho - 1) * maxcol2 * np.linalg.norm(Cemp, 2)
+          + p * (p - 1) * (p - m) / (m * (m - 1) ** 2) * rho * maxcol2 * np.max(np.diag(Cemp))
+          + 2 * p * (p - 1) * (p - m) / (m * (m - 1) ** 2) * xmax2 * fro2 / n
+          + p * (p - m) ** 2 / (m * (m - 1) ** 2) * x4 / n) / n
+    lg = np.log(p / delta)
+    return lg * L / 3 + np.sqrt((lg * L / 3) ** 2 + 2 * lg * s2), Cemp
+
+
+def test_covariance_error_within_theorem_bound():
+    """Sec. V covariance theorem on its own experiment's model (rank-5 data
+    x_i = sum_j kappa_ij lambda_j u_j, lambda = (10, 8, 6, 4, 2)) at p = 256,
+    gamma = 0.3: over seeded masks ||C_n - C_emp||_2 stays below the bound
+    t(delta_2 = 0.01, rho = 1) and, as the paper reports, within an order of
+    magnitude of it; the error falls like 1/sqrt(n) (4n samples: about half)."""
+    p, k, m = 256, 5, 77
+    lam = np.array([10.0, 8.0, 6.0, 4.0, 2.0])
+    rng = np.random.default_rng(1)
+    U, _ = np.linalg.qr(rng.standard_normal((p, k)))
+    errs = {}
+    for n in (2560, 10240):
+        X = ((rng.standard_normal((n, k)) * lam) @ U.T).astype(np.float32)
+        X64 = X.astype(np.float64)
+        t, Cemp = _cov_bound(X64, m, 1.0, 0.01)
+        e = []
+        for seed in range(10):
+            idx, val = oracle.compress_raw(X, m, seed + 1)
+            e.append(np.linalg.norm(oracle.cov(idx, val, p) - Cemp, 2))
+        e = np.array(e)
+        assert e.max() <= t, (n, e.max(), t)
+        assert t / 100 <= e.mean() <= t / 3, (n, e.mean(), t)
+        errs[n] = e.mean()
+    assert 0.35 <= errs[10240] / errs[2560] <= 0.7
