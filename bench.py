@@ -354,13 +354,14 @@ def run_gpu(args, cfg):
 
     stages = ["compress", "gram", "cov_finalize", "topk", "kmeans_prep", "kmeans", "unmix"]
     # library kernels per step: bucket + Gram for the tensor-core modes; top-k
-    # = init + (iters + 1) x panel + (iters + 1) x small Gram + iters x
-    # (Cholesky, apply) + Ritz eigenproblem + Ritz vectors + sign fix, then the
-    # eigenvector un-mix; K-means = start centres + iters x (pass choice,
+    # = init + the float32 panels' diagonal shift (more than 2 iterations) +
+    # (iters + 1) x panel + iters x (Gram, Cholesky, apply) + Rayleigh-Ritz
+    # Gram + Ritz eigenproblem + Ritz vectors + sign fix, then the eigenvector
+    # un-mix; K-means = start centres + iters x (pass choice,
     # full-rebuild pass, incremental pass -- one of the two returns at once --,
     # finalize)
     launches = {"compress": 1, "gram": 1 if args.gram == "fp32" else 2, "cov_finalize": 1,
-                "topk": 4 * max(args.topk_iters, 1) + 6 + 1,
+                "topk": 4 * max(args.topk_iters, 1) + 6 + (1 if args.topk_iters > 2 else 0) + 1,
                 "kmeans_prep": 1, "kmeans": 4 * iters, "unmix": 1}
 
     def step(ev=None):
