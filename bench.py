@@ -58,11 +58,11 @@ PAPER_CONTEXT = {
 UNIT = "samples/s"
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture of this workload (profiles/), valid only
-# while the kernel source still has the digest it had when captured.
+# dominant kernel from one ncu capture of this workload, valid only while the
+# kernel source still has the digest it had when captured.
 KERNEL_TRAFFIC = {
-    # profiles/kmeans_kernel_n4e5_p1024_K10.md: 164.88 MB read + 3.92 MB written
-    # per incremental pass at n = 400,000 (422.0 B per row), scaled to n = 10^6
+    # 164.88 MB read + 3.92 MB written per incremental pass at n = 400,000
+    # (422.0 B per row), scaled to n = 10^6
     "kmeans": {"bytes": 422_000_000, "n": 1_000_000, "p": 1024,
                "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "7710672b8470aee7"},
 }

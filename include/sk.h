@@ -168,9 +168,11 @@ int64_t sk_cov_topk_workspace(int64_t pt, int32_t k);
  * sk_cov_topk.  Shapes whose scratch, sk_cov_topk_workspace(pt, k), exceeds
  * 524,288 doubles (for example pt = 8192 with k > 15) are rejected with
  * SK_EUNSUPPORTED before anything is enqueued.  Every GPU that loads the
- * library holds the array until the process exits.  The first call on a
- * device (with that device current) looks up the array's device address; make
- * that first call before any stream capture.  All calls share the one array
+ * library holds the array until the process exits.  Every call looks up the
+ * array's device address for the current device (a query that allocates
+ * nothing), so the address stays right after a device reset or a new context;
+ * the first call on a device may load the library's device code, so make that
+ * first call before any stream capture.  All calls share the one array
  * and leave their intermediate results in it: calls whose work overlaps on the
  * GPU (different streams without ordering) race and must not be issued. */
 sk_status sk_cov_topk_static(const sk_ctx *ctx, const double *C, int32_t k, int32_t iters,
@@ -455,6 +457,18 @@ sk_status sk_device_status(void *stream);
 
 /* Message for the calling thread's most recent failed call ("" if none). */
 const char *sk_last_error(void);
+
+/* Test hook (no counterpart in the paper): sets the limit of the bounded
+ * mbarrier waits of sk_compress / sk_precondition and of the tensor-core
+ * sk_cov_accumulate modes, in SM clock cycles, for kernels launched after the
+ * call (process-wide; 0 restores the default of 4e9 cycles, about 2 s).  A
+ * short limit makes a wait run out while its copy is still in flight: the
+ * kernel then records the error word that sk_device_status reports as
+ * SK_ETIMEOUT, waits with the default limit for its copies and tensor-core
+ * work in flight, frees its tensor memory and returns, and its outputs are
+ * unspecified.  The next calls with the default limit are unaffected.
+ * Returns SK_EINVAL for cycles < 0. */
+sk_status sk_debug_set_wait_cycles(int64_t cycles);
 
 #ifdef __cplusplus
 }

@@ -96,6 +96,7 @@ def load(path: str | None = None):
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "sk_autotune_compress": (st, [vp, vp, i64, i64, vp, vp, vp, ctypes.POINTER(i32)]),
             "sk_device_status": (st, [vp]),
+            "sk_debug_set_wait_cycles": (st, [i64]),
             "sk_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sigs.items():
@@ -583,6 +584,11 @@ def sk_batch_destroy(b: Batch):
 def sk_device_status(stream=None) -> int:
     """Returns the status code (SK_OK, SK_ETIMEOUT, SK_ECUDA) without raising."""
     return int(load().sk_device_status(_stream(stream)))
+
+
+def sk_debug_set_wait_cycles(cycles: int) -> None:
+    """Limit of the kernels' bounded device waits in SM cycles (0: the default)."""
+    _check("sk_debug_set_wait_cycles", load().sk_debug_set_wait_cycles(int(cycles)))
 
 
 def sk_last_error() -> str:

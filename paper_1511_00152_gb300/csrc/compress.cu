@@ -43,6 +43,7 @@ struct CompressParams {
     int mix;            // 0: no preconditioning (H = D = I), the ablation of Sec. VII
     unsigned int *err;  // device error word (bounded waits)
     int ctas_per_sm;    // autotuned residency cap (0: as many as fit)
+    long long wait_cycles;  // limit of each bounded mbarrier wait (SM clock cycles)
 };
 
 constexpr int kNB = 2;  // staging buffers per warp (one unit in flight ahead)
@@ -54,16 +55,30 @@ struct CompressTask {
     int64_t u_begin;
     int64_t u_end;
 };
+// Default limit of a bounded wait (~2 s at 2 GHz); copies still in flight
+// after a wait ran out are always drained with this limit.
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    const long long deadline = clock64() + kWaitCycles;
+// Waits for the phase of the given parity for at most `limit` cycles.  The
+// first test does not block, so a phase still pending when the limit is
+// already over is reported as a wait that ran out (false).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit) {
+    const long long deadline = clock64() + limit;
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
     for (;;) {
-        uint32_t done;
+        if (clock64() > deadline) return false;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -72,7 +87,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() > deadline) return false;
     }
 }
 
@@ -307,11 +321,13 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
     }
 }
 
-// Shared-memory layout: the fixed part first (mbarriers, then each warp's
-// mask-word window), so that the persistent multi-dataset kernel can run
-// units of different pt back to back on the same barriers; then, per row
-// group, the staging buffers, the virtual Fisher-Yates array and the hit table.
-constexpr size_t kFixedSmem = (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4;
+// Shared-memory layout: the fixed part first (mbarriers, each warp's
+// mask-word window, one abort word per row group), so that the persistent
+// multi-dataset kernel can run units of different pt back to back on the
+// same barriers; then, per row group, the staging buffers, the virtual
+// Fisher-Yates array and the hit table.
+constexpr size_t kFixedSmem = (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4 + (size_t)kWarps * 4;
+static_assert(kFixedSmem % 16 == 0, "bulk-copy destinations stay 16-byte aligned");
 
 template <int L, bool TMA, bool SPLIT = false>
 constexpr size_t compress_smem_bytes() {
@@ -355,6 +371,11 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
     const int grp = warp / G, wg = warp % G;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw) + warp * kNB;
     uint32_t *words = reinterpret_cast<uint32_t *>(smem_raw + (size_t)kWarps * kNB * 8) + warp * 256;
+    // set by any warp of the row group whose wait ran out: the group's warps
+    // share each wait's outcome and leave together (pt > 1024)
+    volatile int *abort_word = reinterpret_cast<volatile int *>(
+                                   smem_raw + (size_t)kWarps * kNB * 8 + (size_t)kWarps * 256 * 4) +
+                               grp;
     unsigned char *var = smem_raw + kFixedSmem;
     float *ybufs = reinterpret_cast<float *>(var) + grp * NBUF * BUF;
     float *ybuf = ybufs;
@@ -382,6 +403,7 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
     const int64_t u_first = u0 + grp;
     bool ok = true;
     if constexpr (TMA) {
+        if (wg == 0 && lane == 0) *abort_word = 0;
         // the buffer may have been read by the previous call's gathers
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         group_sync<G>(grp);
@@ -403,11 +425,23 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
             if (u + stride < nunits)
                 issue_unit<L>(P, u + stride, wg, ybufs + (bsel ^ 1) * BUF + ((L > 10) ? kSeg * wg : 0),
                               smem_u32(mbar + (bsel ^ 1)), lane);
-            if (!mbar_wait_bounded(smem_u32(mbar + bsel), (uint32_t)((kloc >> 1) & 1))) {
+            bool landed = mbar_wait_bounded(smem_u32(mbar + bsel), (uint32_t)((kloc >> 1) & 1),
+                                            P.wait_cycles);
+            if constexpr (G > 1) {
+                // one outcome for the whole row group, so that no warp of it
+                // waits at a group barrier for a warp that has left
+                if (!landed && lane == 0) *abort_word = 1;
+                group_sync<G>(grp);
+                landed = *abort_word == 0;
+            }
+            if (!landed) {
                 if (lane == 0 && P.err) atomicOr(P.err, 2u);
-                // wait (bounded) for the copy still in flight, then stop
+                // before leaving, wait (bounded, default limit) for this
+                // warp's copies still in flight: this unit's and the next one's
+                mbar_wait_bounded(smem_u32(mbar + bsel), (uint32_t)((kloc >> 1) & 1), kWaitCycles);
                 if (u + stride < nunits)
-                    mbar_wait_bounded(smem_u32(mbar + (bsel ^ 1)), (uint32_t)(((kloc + 1) >> 1) & 1));
+                    mbar_wait_bounded(smem_u32(mbar + (bsel ^ 1)), (uint32_t)(((kloc + 1) >> 1) & 1),
+                                      kWaitCycles);
                 ok = false;
                 break;
             }
@@ -796,6 +830,7 @@ static CompressParams make_params(const sk_ctx &c, const float *X, int64_t n, in
     P.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (c.p % 4 == 0) && (ldx % 4 == 0);
     P.err = device_error_word();
     P.ctas_per_sm = c.compress_ctas;
+    P.wait_cycles = wait_limit_cycles();
     return P;
 }
 

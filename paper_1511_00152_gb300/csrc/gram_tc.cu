@@ -62,7 +62,7 @@ constexpr int kTileM = 128;
 constexpr int kSegmentRows = 1 << 18;     // rows per work unit (FP32 registers, then FP64)
 constexpr int kChunkSlabs = 8;            // slabs per tensor-core accumulation chain
 constexpr int kBlk = 128;                  // column block of the bucketing
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: default limit, and drains
 
 struct TcParams {
     const int32_t *idx;
@@ -83,6 +83,7 @@ struct TcParams {
     const int2 *bkt;      // bucketed entries: (block << 14 | tile byte offset, value bits)
     const int *boff;      // per slab: nblk + 1 bucket starts (relative to the slab)
     double *G;
+    long long wait_cycles;  // limit of the CTA's pipeline waits (SM clock cycles)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -99,10 +100,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 // Bounded wait for the phase of the given parity; false on expiry or abort.
+// The first test does not block, so a phase still pending once the deadline
+// has passed counts as a wait that ran out.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long deadline,
                                           volatile int *abort_flag) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
     for (;;) {
-        uint32_t done;
+        if (*abort_flag) return false;
+        if (clock64() > deadline) return false;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -111,8 +124,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (*abort_flag) return false;
-        if (clock64() > deadline) return false;
     }
 }
 
@@ -309,7 +320,7 @@ __device__ __forceinline__ void gram_tc_body(const TcParams &P, int bid) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const long long deadline = clock64() + kWaitCycles;
+    const long long deadline = clock64() + P.wait_cycles;
     const uint32_t done_bar = smem_u32(bars + 2 * S);
 
     if (warp == kLoaderWarp) {
@@ -553,7 +564,7 @@ __device__ __forceinline__ void gram_tc_body(const TcParams &P, int bid) {
         // ---------------- epilogue: TMEM -> FP64 Gram
         const bool have = nslabs > 0;
         bool drained = false;
-        if (have) drained = mbar_wait(done_bar, 0u, deadline + kWaitCycles, abort_flag) || false;
+        if (have) drained = mbar_wait(done_bar, 0u, deadline + P.wait_cycles, abort_flag);
         if (have && !drained) {
             // a stalled pipeline: give the issued MMAs one more bounded wait
             // (without the abort short-cut) so TMEM is idle before it is freed
@@ -634,6 +645,7 @@ static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const 
     if (P.N == 128 && !P.hilo) P.nstages = 6;
     if (P.N == 128 && P.hilo) P.nstages = 3;
     P.G = G;
+    P.wait_cycles = wait_limit_cycles();
     P.nblk = P.pt / kBlk;
     // workspace: bucketed entries (8 bytes each, 64 m per slab), then offsets
     nslab = (n + kSlab - 1) / kSlab;

@@ -2,6 +2,7 @@
 // then one or more kernel launches on the caller's stream.  No exception
 // crosses the boundary; every failure returns a status and records a message
 // for sk_last_error().
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,11 @@ namespace sk {
 void set_last_error(const char *msg) {
     std::snprintf(g_msg, sizeof(g_msg), "%s", msg ? msg : "");
 }
+
+constexpr long long kDefaultWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+std::atomic<long long> g_wait_cycles{kDefaultWaitCycles};
+
+long long wait_limit_cycles() { return g_wait_cycles.load(std::memory_order_relaxed); }
 }  // namespace sk
 
 extern "C" {
@@ -548,5 +554,13 @@ sk_status sk_device_status(void *stream) {
 }
 
 const char *sk_last_error(void) { return g_msg; }
+
+sk_status sk_debug_set_wait_cycles(int64_t cycles) {
+    if (cycles < 0) return fail(SK_EINVAL, "sk_debug_set_wait_cycles: cycles must be >= 0");
+    sk::g_wait_cycles.store(cycles == 0 ? sk::kDefaultWaitCycles : (long long)cycles,
+                            std::memory_order_relaxed);
+    g_msg[0] = 0;
+    return SK_OK;
+}
 
 }  // extern "C"

@@ -226,9 +226,12 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters,
                         double *evals, double *U, double *work, cudaStream_t s);
 int64_t topk_workspace(int64_t pt, int k);
 // Fixed top-k scratch (a static device array of topk_static_capacity() doubles):
-// its device address for the current device (looked up on first use).
+// its device address for the current device (looked up on every call).
 int64_t topk_static_capacity();
 cudaError_t topk_static_scratch(double **out);
+// Limit of the kernels' bounded device waits, in SM clock cycles (default
+// 4e9, about 2 s; sk_debug_set_wait_cycles changes it for later launches).
+long long wait_limit_cycles();
 // Reads and clears the device error word of the kernels with bounded waits
 // (bit 0: an mbarrier wait ran out).  Returns cudaSuccess or the copy error.
 cudaError_t take_device_error(unsigned int *flag);

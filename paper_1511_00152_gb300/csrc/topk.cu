@@ -22,7 +22,6 @@
 // and polished by a few float64 Jacobi sweeps (whose rotation angles are
 // again float32 estimates; each rotation itself is orthogonal to float64
 // rounding, so only the convergence rate of the last sweeps changes).
-#include <mutex>
 
 #include "sk_internal.cuh"
 
@@ -724,30 +723,21 @@ __global__ void __launch_bounds__(256) sign_fix_kernel(int64_t pt, double *U) {
 // One array per device that loads the library, held until the process exits.
 // Host code must not pass g_topk_scratch itself to a kernel (on the host the
 // name is only a stand-in for the device symbol); its device address is looked
-// up once per device with cudaGetSymbolAddress, with that device current.
+// up with cudaGetSymbolAddress on every call, with the caller's device current,
+// so that no stale address survives a device reset or a new context.
 namespace {
 constexpr int64_t kTopkStaticDoubles = 512 * 1024;  // 4 MiB
 static __device__ __align__(256) double g_topk_scratch[kTopkStaticDoubles];
-std::mutex g_topk_scratch_mu;
-double *g_topk_scratch_ptr[128] = {};
 }  // namespace
 
 int64_t topk_static_capacity() { return kTopkStaticDoubles; }
 
 cudaError_t topk_static_scratch(double **out) {
     *out = nullptr;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_topk_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_topk_scratch_mu);
-    if (!g_topk_scratch_ptr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_topk_scratch);
-        if (e != cudaSuccess) return e;
-        g_topk_scratch_ptr[dev] = static_cast<double *>(ptr);
-    }
-    *out = g_topk_scratch_ptr[dev];
+    *out = static_cast<double *>(ptr);
     return cudaSuccess;
 }
 

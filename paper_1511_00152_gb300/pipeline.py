@@ -50,17 +50,23 @@ class KMeansState:
                                     self.nk, dist=self.dist, changed=self.changed, stream=stream)
         sk.sk_kmeans_finalize(ctx, self.S, self.cnt, self.mu, stream=stream)
 
-    def run(self, idx, val, mu0, iters: int, use_graph: bool = True):
+    def run(self, idx, val, mu0, iters: int, use_graph: bool = True, history=None):
         """iters iterations from the preconditioned-domain centres mu0 (K x pt).
 
         With use_graph, the loop is captured once as a CUDA graph and replayed
-        (the same kernels, one launch for the whole loop)."""
+        (the same kernels, one launch for the whole loop).  history (device
+        int32 iters x n, optional) receives each iteration's labels."""
         self.mu.copy_(mu0)
+        if history is not None and tuple(history.shape) != (iters, self.n):
+            raise ValueError("history must be iters x n")
         if not use_graph or iters == 0:
             for it in range(iters):
                 self.iteration(idx, val, first=(it == 0))
+                if history is not None:
+                    history[it].copy_(self.labels)
             return self.labels, self.mu
-        key = (idx.data_ptr(), val.data_ptr(), idx.shape[0], iters)
+        key = (idx.data_ptr(), val.data_ptr(), idx.shape[0], iters,
+               None if history is None else history.data_ptr())
         if self.graph is None or self._graph_args != key:
             # warm the launch configuration outside capture, then capture
             s = torch.cuda.Stream()
@@ -75,6 +81,8 @@ class KMeansState:
             with torch.cuda.graph(g):
                 for it in range(iters):
                     self.iteration(idx, val, first=(it == 0))
+                    if history is not None:
+                        history[it].copy_(self.labels)
             self.graph, self._graph_args = g, key
             self.mu.copy_(mu0)
         self.graph.replay()

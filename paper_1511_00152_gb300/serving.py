@@ -36,6 +36,7 @@ class Request:
     make_x: object = None     # callable(torch.cuda.Stream) -> device tensor n x p (generated)
     x: object = None          # or a device / pinned host tensor n x p
     arrival: float = 0.0      # seconds, relative to the start of run()
+    labels_out: object = None  # optional device int32 tensor (n): the rows' K-means labels
     # filled by the server
     admitted: float = -1.0
     done_event: object = None
@@ -128,8 +129,9 @@ class Server:
             idx, val = slot.idx[:n], slot.val[:n]
             sk.sk_compress(self.ctx, x, row0=req.row0, idx=idx, val=val, stream=s)
             sk.sk_cov_accumulate(self.ctx, self.mode, idx, val, st.G, work=slot.work, stream=s)
-            sk.sk_kmeans_assign(self.ctx, idx, val, st.mu, labels=slot.labels[:n], stream=s)
-            sk.sk_kmeans_update(self.ctx, idx, val, slot.labels[:n], st.K, st.S, st.cnt, st.nk,
+            labels = slot.labels[:n] if req.labels_out is None else req.labels_out
+            sk.sk_kmeans_assign(self.ctx, idx, val, st.mu, labels=labels, stream=s)
+            sk.sk_kmeans_update(self.ctx, idx, val, labels, st.K, st.S, st.cnt, st.nk,
                                 stream=s)
             req.done_event = torch.cuda.Event(enable_timing=True)
             req.done_event.record(s)
@@ -138,8 +140,11 @@ class Server:
 
     def run(self, requests, realtime: bool = False):
         """Serve the requests (sorted by arrival).  With realtime, a request is
-        not admitted before its arrival time; otherwise arrivals only order
-        the queue.  Returns the completed requests."""
+        not admitted before its arrival time and its latency_ms runs from its
+        arrival (queueing included) to the end of its device work.  Otherwise
+        arrivals only order the queue and latency_ms is the request's device
+        time alone (start to end of its work on its slot's stream).  Returns
+        the completed requests."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         for r in pending:
             r.bytes = self.request_bytes(r.n)
@@ -154,10 +159,12 @@ class Server:
         active = 0
         while pending or active:
             now = time.perf_counter() - t0
+            progressed = False
             # retire finished work (non-blocking)
             for slot in self.slots:
                 r = slot.req
                 if r is not None and r.done_event.query():
+                    progressed = True
                     r.latency_ms = r.start_event.elapsed_time(r.done_event) + \
                         max(0.0, (r.admitted - host_arrival[id(r)]) * 1e3)
                     self.in_flight_bytes -= r.bytes
@@ -180,8 +187,11 @@ class Server:
                 self.peak_bytes = max(self.peak_bytes, self.in_flight_bytes)
                 self._launch(slot, r)
                 active += 1
-            if active and all(s.req is not None for s in self.slots):
-                time.sleep(0)  # yield; completion is polled with event queries
+                progressed = True
+            if not progressed:
+                # nothing retired or admitted (all slots busy, the next request
+                # not yet arrived, or the budget full): yield before polling again
+                time.sleep(0 if active else 1e-4)
         torch.cuda.synchronize()
         return self.completed
 

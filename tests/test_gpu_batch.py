@@ -153,3 +153,47 @@ def test_single_handle_autotuners():
     U0, U1 = torch.triu(G0), torch.triu(G)
     assert (torch.linalg.norm(U1 - U0) / torch.linalg.norm(U0)).item() <= 1e-6
     assert sk.sk_device_status() == sk.SK_OK
+
+
+def test_batch_matches_oracle():
+    """Every data set of a split-BF16 batch (ragged p, m, K and n in one
+    launch per stage) against the FP64 oracle on its own rows: idx bit-exact,
+    val <= 1e-5 ||x_r||; the Gram and C_n to 1e-5 relative Frobenius; the
+    first K-means pass from the seeded start against the oracle's assignment
+    and sums (counts and sizes exact, centres 1e-5, over the clusters no
+    near-tie row touched; tests/kmeans_trace.py)."""
+    import kmeans_trace
+    import oracle
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import pipeline
+    sets = [(2500, 256, 13, 5, 21), (1300, 1000, 51, 10, 22), (700, 4096, 205, 20, 23),
+            (333, 2048, 41, 7, 24)]
+    ds = []
+    for (n, p, m, K, seed) in sets:
+        X, _, _ = synth.mixture_device(n, p, min(K, 10), seed)
+        ds.append(dict(X=X, m=m, K=K, seed=seed))
+    br = pipeline.BatchRun(ds, mode=sk.SK_GRAM_BF16X3)
+    br.compress_and_cov()
+    br.init_centres()
+    sk.sk_batch_kmeans_reset(br.batch)
+    sk.sk_batch_kmeans_step(br.batch, incremental=False)
+    sk.sk_batch_kmeans_finalize(br.batch)
+    torch.cuda.synchronize()
+    for e, (n, p, m, K, seed) in zip(br.ds, sets):
+        X = e["X"].cpu().numpy()
+        oi, ov = oracle.compress(X, m, seed)
+        assert np.array_equal(e["idx"].cpu().numpy(), oi)
+        nrm = np.linalg.norm(X.astype(np.float64), axis=1)
+        assert np.all(np.abs(e["val"].cpu().numpy() - ov).max(axis=1) <= 1e-5 * nrm)
+        pt = e["ctx"].pt
+        Go = oracle.gram(oi, ov, pt)
+        Gg = e["G"].cpu().numpy()
+        assert np.linalg.norm(np.triu(Gg) - np.triu(Go)) <= 1e-5 * np.linalg.norm(np.triu(Go))
+        C = sk.sk_cov_finalize(e["ctx"], e["G"], n).cpu().numpy()
+        Co = oracle.cov_finalize(Go, n, m)
+        assert np.linalg.norm(C - Co) <= 1e-5 * np.linalg.norm(Co)
+        mu0 = oracle.precondition(e["Xsel"].cpu().numpy(), seed)
+        trace = kmeans_trace.oracle_trace(oi, ov, mu0, pt, 1)
+        kmeans_trace.check_against_trace([e["labels"].cpu().numpy()], e["mu"].cpu().numpy(),
+                                         e["cnt"].cpu().numpy(), e["nk"].cpu().numpy(), trace, K)
+    assert sk.sk_device_status() == sk.SK_OK

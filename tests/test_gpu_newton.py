@@ -17,14 +17,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
-def probe(tmp_path_factory):
-    out = str(tmp_path_factory.mktemp("nr") / "libnrprobe.so")
+def newton(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("nr") / "libnewton_eval.so")
     subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
                     "-shared", "-Xcompiler", "-fPIC", "-o", out,
-                    os.path.join(HERE, "gpu_probe", "nr_probe.cu")], check=True)
+                    os.path.join(HERE, "gpu_fixture", "newton_eval.cu")], check=True)
     lib = ctypes.CDLL(out)
-    lib.nr_probe.restype = ctypes.c_int
-    lib.nr_probe.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.newton_eval.restype = ctypes.c_int
+    lib.newton_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -32,7 +32,7 @@ def _ulps(a, ref):
     return np.abs(a - ref) / np.spacing(np.abs(ref))
 
 
-def test_newton_rsqrt_rcp_within_4_ulp(probe):
+def test_newton_rsqrt_rcp_within_4_ulp(newton):
     rng = np.random.default_rng(5)
     n = 200_000
     mant = rng.uniform(1.0, 2.0, n)
@@ -44,7 +44,7 @@ def test_newton_rsqrt_rcp_within_4_ulp(probe):
     xd = torch.as_tensor(x, device="cuda")
     rs = torch.empty_like(xd)
     rc = torch.empty_like(xd)
-    assert probe.nr_probe(ctypes.c_void_p(xd.data_ptr()), x.size, ctypes.c_void_p(rs.data_ptr()),
+    assert newton.newton_eval(ctypes.c_void_p(xd.data_ptr()), x.size, ctypes.c_void_p(rs.data_ptr()),
                           ctypes.c_void_p(rc.data_ptr())) == 0
     rs, rc = rs.cpu().numpy(), rc.cpu().numpy()
     pos = x > 0

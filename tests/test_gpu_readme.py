@@ -1,5 +1,6 @@
-"""The README's usage example runs as written (smaller n) and returns results
-of the documented shapes."""
+"""The documented usage example (compress, covariance, top-k PCA, K-means,
+un-mixed centres) runs as written at a smaller n and returns results of the
+documented shapes."""
 import pytest
 import torch
 

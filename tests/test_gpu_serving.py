@@ -114,3 +114,57 @@ def test_stream_equals_one_batch():
     assert np.array_equal(cnt, c1.cpu().numpy()) and np.array_equal(nk, n1.cpu().numpy())
     C = srv.streams[0].covariance()
     assert torch.allclose(C, C.T)
+
+
+def test_served_stream_matches_oracle():
+    """A stream served in the mix (three slots, its chunks interleaved with
+    another stream's, uneven chunk sizes and row offsets) against the FP64
+    oracle on the same rows: the split-BF16 Gram to 1e-5 relative Frobenius,
+    C_n likewise; the K-means sums against the oracle's assignment to the
+    stream's centres (counts and sizes exact, S to 1e-5, over the clusters no
+    near-tie row touched; tests/kmeans_trace.py)."""
+    import kmeans_trace
+    import oracle
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import serving
+    seed, seeds, rows = 13, [55, 66], 30000
+    srv = serving.Server(P, M, seed, slots=3, max_rows=16384, mode=sk.SK_GRAM_BF16X3)
+    X0s = {}
+    for sid, sseed in enumerate(seeds):
+        X0s[sid] = synth.lowrank_mixture_chunk_device(K, P, sseed, 10**9)
+        srv.open_stream(sid, sk.sk_precondition(srv.ctx, X0s[sid]))
+    reqs = _requests(serving, seeds, rows)
+    rng = np.random.default_rng(1)
+    lab_g = torch.full((rows,), -1, dtype=torch.int32, device="cuda")
+    for r in reqs:
+        r.arrival = float(rng.uniform(0, 1))
+        if r.stream_id == 0:
+            r.labels_out = lab_g[r.row0:r.row0 + r.n]
+    srv.run(reqs)
+    G, S, cnt, nk, nrows = _state(srv.streams[0])
+    assert nrows == rows
+    # the oracle's run of stream 0: its chunks' rows (drawn again from the
+    # seeded generator), compressed at their global row offsets
+    oi_parts, ov_parts = [], []
+    for (r0, n) in _chunks(0, rows, seeds[0]):
+        Xc = synth.lowrank_mixture_chunk_device(n, P, seeds[0], r0).cpu().numpy()
+        ci, cv = oracle.compress(Xc, M, seed, row0=r0)
+        oi_parts.append(ci)
+        ov_parts.append(cv)
+    oi, ov = np.concatenate(oi_parts), np.concatenate(ov_parts)
+    pt = srv.ctx.pt
+    Go = oracle.gram(oi, ov, pt)
+    rel = np.linalg.norm(np.triu(G) - np.triu(Go)) / np.linalg.norm(np.triu(Go))
+    assert rel <= 1e-5, rel
+    C = srv.streams[0].covariance().cpu().numpy()
+    Co = oracle.cov_finalize(Go, rows, M)
+    assert np.linalg.norm(C - Co) <= 1e-5 * np.linalg.norm(Co)
+    mu_o = oracle.precondition(X0s[0].cpu().numpy(), seed)
+    trace = kmeans_trace.oracle_trace(oi, ov, mu_o, pt, 1)
+    keep, _ = kmeans_trace.untouched([lab_g.cpu().numpy()], trace, K)
+    assert keep.sum() >= K // 2
+    assert np.array_equal(cnt[keep], trace["counts"][keep])
+    assert np.array_equal(nk[keep], trace["nk"][keep])
+    So = np.where(trace["counts"] > 0, trace["mu"] * trace["counts"], 0.0)
+    assert np.abs(S[keep] - So[keep]).max() <= 1e-5 * np.abs(So).max()
+    assert sk.sk_device_status() == sk.SK_OK
