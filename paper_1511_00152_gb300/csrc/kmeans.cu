@@ -214,7 +214,8 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
                 // leaves cluster old and joins cluster label (exact in FP64 for
                 // float inputs up to rounding of the running sums)
                 old = __shfl_sync(kFull, old, (lead < 32) ? lead : lane);
-                const bool moved = row_ok && kl == 0 && old != label;
+                const bool moved = row_ok && kl == 0 && old != label &&
+                                   (unsigned)label < (unsigned)P.K;
                 const unsigned mv = __ballot_sync(kFull, moved);
                 if (P.changed && lane == 0 && mv)
                     atomicAdd(P.changed, (unsigned long long)__popc(mv));
@@ -573,6 +574,462 @@ cudaError_t launch_kpl(KmParams &P, cudaStream_t s) {
     return launch_stage<KPL, false, false>(P, 0, budget, s);
 }
 
+// ---- one lane per row part, all K centres per lane (K <= 32)
+//
+// A half-warp holds NP = ceil(K/2) rows and C = 16 / NP lanes per row (one
+// per "copy").  Lane (c, ph) owns row ph of its half-warp and the entries
+// t = c, c + C, ... of that row, and accumulates the restricted distances to
+// all K centres (NP packed pairs) for them; the C partial sums of a row are
+// added with shuffles at the end.  Coordinate j owns one 32-word line of
+// shared memory with C copies of its Kpad = 2 NP centre values, copy c at
+// pair positions c NP .. c NP + NP - 1.  At unrolled step q, lane (c, ph)
+// reads pair (q + ph) mod NP of copy c: the 16 lanes of a half-warp then hit
+// 16 distinct bank pairs whatever their rows' coordinates, so each centre
+// load is one wavefront per half-warp and carries 8 bytes for every lane.
+// The rotation makes accumulator slot q of lane (c, ph) hold centre pair
+// (q + ph) mod NP; all lanes of a row share ph, so their slots line up.
+// The rows are staged per warp as (idx, val) pairs at a row stride S >= m
+// chosen so that a half-warp's stage read touches distinct bank pairs too
+// ((ph S + c) mod 16 distinct over its lanes; S = C (mod 16) always works).
+struct RcParams {
+    const int32_t *idx;
+    const float *val;
+    int64_t n;
+    int m, pt, K, S;
+    uint32_t minv;  // floor(2^32 / m) + 1 (m >= 2): e / m = umulhi(e, minv) for e m < 2^32
+    const float *mu;
+    int32_t *labels;
+    float *dist;
+    double *Ssum;
+    int32_t *cnt;
+    int64_t *nk;
+    unsigned long long *changed;  // rows whose label changed (may be NULL)
+    int do_update;                // 0 none, 2 incremental (changed rows only)
+    const int64_t *mode;          // adaptive passes: run only if *mode == expect
+    int expect;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t lds64(uint32_t addr) {
+    uint64_t v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+// Threads per CTA of the rotated-copies pass: up to 32 warps while a lane's
+// NP accumulator pairs and offsets fit 64 registers, 20 warps above that.
+// (A row whose distances are all NaN keeps the label 0x7fffffff, which every
+// update skips.)
+template <int NP>
+constexpr int rc_max_threads() { return NP <= 9 ? 1024 : 640; }
+
+template <int NP>
+__global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParams P) {
+    constexpr int C = 16 / NP;  // lanes per row
+    constexpr int RW = 2 * NP;  // rows per warp
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (P.mode && *P.mode != P.expect) return;  // the other kind of pass runs
+    float *tab = reinterpret_cast<float *>(smem_raw);
+    int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + (size_t)P.pt * 128);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        // word w of line j: copy w / (2 NP), centre 2 ((w / 2) mod NP) + (w & 1);
+        // eight loads in flight per thread before their stores
+        constexpr int kU = 8;
+        for (int e0 = tid; e0 < P.pt * 32; e0 += kU * blockDim.x) {
+            float x[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + u * blockDim.x;
+                const int j = e >> 5, w = e & 31, b = w >> 1;
+                x[u] = 0.f;
+                if (e < P.pt * 32 && b < C * NP) {
+                    const int cc = b / NP;
+                    const int k = 2 * (b - cc * NP) + (w & 1);
+                    if (k < P.K) x[u] = __ldg(P.mu + (int64_t)k * P.pt + j);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < P.pt * 32) tab[e] = x[u];
+            }
+        }
+    }
+    __syncthreads();
+
+    const int h = lane >> 4, sl = lane & 15;
+    const bool used = sl < C * NP;
+    const int c = used ? sl / NP : 0;
+    const int ph = used ? sl - c * NP : 0;
+    const int rw = h * NP + ph;          // row of this lane within the warp's group
+    const int lead = h * 16 + ph;        // lane c = 0 of this row
+    uint32_t off[NP];                    // byte offsets of the lane's NP pairs in a line
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        int pi = q + ph;
+        if (pi >= NP) pi -= NP;
+        off[q] = smem_u32(tab) + 8u * (uint32_t)(c * NP + pi);
+    }
+    const int m = P.m, S = P.S;
+    const int pmask = P.pt - 1;
+    int2 *stage = stage_all + (size_t)warp * RW * S;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool track_old = P.do_update == 2 || P.changed != nullptr;
+
+    for (int64_t base = gwarp * RW; base < P.n; base += nwarps * RW) {
+        const int rows_here = (int)((P.n - base) < RW ? (P.n - base) : RW);
+        {
+            // the group's rows are contiguous in the ELL arrays: coalesced
+            // loads, eight per lane in flight before their stores
+            constexpr int kU = 8;
+            const int total = rows_here * m;
+            const int32_t *gi = P.idx + base * m;
+            const float *gv = P.val + base * m;
+            for (int e0 = lane; e0 < total; e0 += 32 * kU) {
+                int2 x[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + 32 * u;
+                    if (e < total) x[u] = make_int2(__ldg(gi + e), __float_as_int(__ldg(gv + e)));
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + 32 * u;
+                    if (e < total) {
+                        const int r = m == 1 ? e : (int)__umulhi((uint32_t)e, P.minv);
+                        stage[r * S + (e - r * m)] = x[u];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        const int64_t i = base + rw;
+        const bool row_ok = used && rw < rows_here;
+        int old = -1;
+        if (track_old && row_ok && c == 0) old = P.labels[i];
+        uint64_t acc[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+        const int2 *rs = stage + rw * S;
+        if (row_ok) {
+#pragma unroll 2
+            for (int t = c; t < m; t += C) {
+                const int2 iv = rs[t];
+                const uint32_t jb = (uint32_t)(iv.x & pmask) << 7;
+                const float v = __int_as_float(iv.y);
+                const uint64_t vv = pack2(v, v);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) acc[q] = sqacc2(sub2(vv, lds64(off[q] + jb)), acc[q]);
+            }
+        }
+        // the C partial sums of a row, into its lane c = 0 (the row's lanes
+        // are NP apart inside the half-warp)
+#pragma unroll
+        for (int cc = 1; cc < C; ++cc) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const uint64_t o = __shfl_down_sync(kFull, acc[q], cc * NP);
+                if (c == 0) {
+                    uint64_t a;
+                    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(a) : "l"(acc[q]), "l"(o));
+                    acc[q] = a;
+                }
+            }
+        }
+        // argmin over the K centres (ties to the smaller k); slot q holds pair
+        // (q + ph) mod NP
+        float bd = INFINITY;
+        int bk = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            int pi = q + ph;
+            if (pi >= NP) pi -= NP;
+            const int k0 = 2 * pi;
+            const float d0 = __uint_as_float((uint32_t)acc[q]);
+            const float d1 = __uint_as_float((uint32_t)(acc[q] >> 32));
+            if (k0 < P.K && (d0 < bd || (d0 == bd && k0 < bk))) {
+                bd = d0;
+                bk = k0;
+            }
+            if (k0 + 1 < P.K && (d1 < bd || (d1 == bd && k0 + 1 < bk))) {
+                bd = d1;
+                bk = k0 + 1;
+            }
+        }
+        const int label = __shfl_sync(kFull, bk, lead);
+        old = __shfl_sync(kFull, old, lead);
+        if (row_ok && c == 0) {
+            P.labels[i] = label;
+            if (P.dist) P.dist[i] = bd;
+        }
+        const bool moved = row_ok && old != label && (unsigned)label < (unsigned)P.K;
+        if (P.changed) {
+            const unsigned mv = __ballot_sync(kFull, moved && c == 0);
+            if (lane == 0 && mv) atomicAdd(P.changed, (unsigned long long)__popc(mv));
+        }
+        if (P.do_update == 2 && moved) {
+            // incremental sums: the row leaves cluster old and joins label
+            // (its C lanes move their own entries)
+            for (int t = c; t < m; t += C) {
+                const int2 iv = rs[t];
+                const int j = iv.x & pmask;
+                const double v = (double)__int_as_float(iv.y);
+                atomicAdd(P.Ssum + (int64_t)label * P.pt + j, v);
+                atomicAdd(P.cnt + (int64_t)label * P.pt + j, 1);
+                if ((unsigned)old < (unsigned)P.K) {
+                    atomicAdd(P.Ssum + (int64_t)old * P.pt + j, -v);
+                    atomicAdd(P.cnt + (int64_t)old * P.pt + j, -1);
+                }
+            }
+            if (c == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + label), 1ull);
+                if ((unsigned)old < (unsigned)P.K)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + old),
+                              (unsigned long long)(-1LL));
+            }
+        }
+        __syncwarp();  // the stage is rewritten by the next group
+    }
+}
+
+template <int NP>
+cudaError_t launch_rc_np(const RcParams &P, int warps, size_t smem, cudaStream_t s) {
+    auto kern = kmeans_rc_kernel<NP>;
+    if (warps > rc_max_threads<NP>() / 32) {
+        warps = rc_max_threads<NP>() / 32;
+        smem = (size_t)P.pt * 128 + (size_t)warps * 2 * NP * P.S * 8;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t groups = (P.n + 2 * NP - 1) / (2 * NP);
+    int64_t blocks = (groups + warps - 1) / warps;
+    if (blocks > sms) blocks = sms;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, warps * 32, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+// ---- the sums of a full rebuild from finished labels (Eq. (mu_update_one))
+//
+// After the rotated-copies assignment has written every row's label, this
+// pass adds each entry to S[label][idx] and cnt[label][idx] and each row to
+// nk[label], in CTA-private shared-memory sums (float S, int32 counts)
+// flushed to the caller's float64 / int32 / int64 sums with one atomic per
+// touched slot.  A warp takes 32 consecutive rows at a time: lane l holds the
+// label of row l and the rows' m entries are read flat and coalesced, each
+// entry's label passed by a shuffle.
+struct SumParams {
+    const int32_t *idx;
+    const float *val;
+    const int32_t *labels;
+    int64_t n;
+    int m, pt, K;
+    uint32_t minv;  // floor(2^32 / m) + 1 (m >= 2)
+    double *Ssum;
+    int32_t *cnt;
+    int64_t *nk;
+    const int64_t *mode;  // adaptive passes: run only if *mode == expect
+    int expect;
+};
+
+__global__ void __launch_bounds__(kThreads) kmeans_sums_kernel(SumParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (P.mode && *P.mode != P.expect) return;
+    const int KP = P.K * P.pt;
+    float *sS = reinterpret_cast<float *>(smem_raw);
+    int32_t *sC = reinterpret_cast<int32_t *>(smem_raw + (size_t)KP * 4);
+    int32_t *snk = reinterpret_cast<int32_t *>(smem_raw + (size_t)KP * 8);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < KP; e += blockDim.x) {
+        sS[e] = 0.f;
+        sC[e] = 0;
+    }
+    for (int e = tid; e < P.K; e += blockDim.x) snk[e] = 0;
+    __syncthreads();
+    const int m = P.m, pmask = P.pt - 1;
+    const int wpb = blockDim.x >> 5;
+    const int64_t nchunks = (P.n + 31) / 32;
+    for (int64_t ch = (int64_t)blockIdx.x * wpb + warp; ch < nchunks;
+         ch += (int64_t)gridDim.x * wpb) {
+        const int64_t r0 = ch * 32;
+        const int rows = (int)((P.n - r0) < 32 ? (P.n - r0) : 32);
+        const int lab = lane < rows ? __ldg(P.labels + r0 + lane) : -1;
+        const bool lab_ok = (unsigned)lab < (unsigned)P.K;
+        {
+            // rows of one cluster within the 32: one atomic per cluster
+            const unsigned grp = __match_any_sync(kFull, lab);
+            if (lab_ok && (grp & lanemask_lt()) == 0) atomicAdd(snk + lab, __popc(grp));
+        }
+        const int total = rows * m;
+        const int32_t *gi = P.idx + r0 * m;
+        const float *gv = P.val + r0 * m;
+        constexpr int kU = 4;
+        for (int e0 = lane; e0 - lane < total; e0 += 32 * kU) {
+            int jx[kU];
+            float vx[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + 32 * u;
+                jx[u] = 0;
+                vx[u] = 0.f;
+                if (e < total) {
+                    jx[u] = __ldg(gi + e);
+                    vx[u] = __ldg(gv + e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + 32 * u;
+                const int r = e < total ? (m == 1 ? e : (int)__umulhi((uint32_t)e, P.minv)) : 0;
+                const int le = __shfl_sync(kFull, lab, r);
+                if (e < total && (unsigned)le < (unsigned)P.K) {
+                    const int slot = le * P.pt + (jx[u] & pmask);
+                    atomicAdd(sS + slot, vx[u]);
+                    atomicAdd(sC + slot, 1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < KP; e += blockDim.x) {
+        const int c = sC[e];
+        const float x = sS[e];
+        if (x != 0.f) atomicAdd(P.Ssum + e, (double)x);
+        if (c) atomicAdd(P.cnt + e, c);
+    }
+    for (int e = tid; e < P.K; e += blockDim.x)
+        if (snk[e]) atomicAdd(reinterpret_cast<unsigned long long *>(P.nk + e),
+                              (unsigned long long)(long long)snk[e]);
+}
+
+// Launches kmeans_sums_kernel if its shared-memory sums fit; *used tells
+// whether it did.
+cudaError_t launch_sums(const KmParams &Q, cudaStream_t s, bool *used) {
+    *used = false;
+    int dev = 0, smem_max = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)Q.K * Q.pt * 8 + (((size_t)Q.K * 4 + 15) & ~(size_t)15);
+    if (smem > (size_t)smem_max) return cudaSuccess;
+    SumParams P;
+    P.idx = Q.idx;
+    P.val = Q.val;
+    P.labels = Q.labels;
+    P.n = Q.n;
+    P.m = Q.m;
+    P.pt = Q.pt;
+    P.K = Q.K;
+    P.minv = Q.m >= 2 ? (uint32_t)(0x100000000ull / (uint64_t)Q.m + 1) : 0u;
+    P.Ssum = Q.S;
+    P.cnt = Q.cnt;
+    P.nk = Q.nk;
+    P.mode = Q.mode;
+    P.expect = Q.expect;
+    cudaError_t e = cudaFuncSetAttribute(kmeans_sums_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeans_sums_kernel, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t chunks = (Q.n + 31) / 32;
+    int64_t blocks = (chunks + kWarpsK - 1) / kWarpsK;
+    if (blocks > (int64_t)sms * per_sm) blocks = (int64_t)sms * per_sm;
+    if (blocks < 1) blocks = 1;
+    *used = true;
+    kmeans_sums_kernel<<<(unsigned)blocks, kThreads, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+// Launches the rotated-copies pass if it applies (K <= 32, no full-rebuild
+// sums, the table and at least eight warps' staging fit shared memory);
+// *used tells whether it did.
+cudaError_t launch_rc(const KmParams &Q, cudaStream_t s, bool *used) {
+    *used = false;
+    if (!Q.do_assign || Q.K > 32) return cudaSuccess;
+    const int NP = (Q.K + 1) / 2;
+    const int C = 16 / NP;
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // stage row stride: the smallest S >= m for which the bank pairs
+    // (ph S + c) mod 16 of a half-warp's lanes (ph < NP, c < C) are distinct
+    int S = Q.m;
+    for (;; ++S) {
+        unsigned seen = 0;
+        bool ok = true;
+        for (int ph = 0; ph < NP && ok; ++ph)
+            for (int c = 0; c < C && ok; ++c) {
+                const unsigned bit = 1u << ((ph * S + c) & 15);
+                ok = !(seen & bit);
+                seen |= bit;
+            }
+        if (ok) break;
+    }
+    const size_t table = (size_t)Q.pt * 128;
+    const size_t per_warp = (size_t)2 * NP * S * 8;
+    if (table + 8 * per_warp > (size_t)smem_max) return cudaSuccess;
+    int warps = (int)(((size_t)smem_max - table) / per_warp);
+    if (warps > kWarpsK) warps = kWarpsK;
+    RcParams P;
+    P.idx = Q.idx;
+    P.val = Q.val;
+    P.n = Q.n;
+    P.m = Q.m;
+    P.pt = Q.pt;
+    P.K = Q.K;
+    P.S = S;
+    P.minv = Q.m >= 2 ? (uint32_t)(0x100000000ull / (uint64_t)Q.m + 1) : 0u;
+    P.mu = Q.mu;
+    P.labels = Q.labels;
+    P.dist = Q.dist;
+    P.Ssum = Q.S;
+    P.cnt = Q.cnt;
+    P.nk = Q.nk;
+    P.changed = Q.changed;
+    P.do_update = Q.do_update == 2 ? 2 : 0;
+    P.mode = Q.mode;
+    P.expect = Q.expect;
+    const size_t smem = table + (size_t)warps * per_warp;
+    if (Q.do_update == 1) {
+        // a full rebuild: this assignment, then the sums from its labels
+        const size_t sums_b = (size_t)Q.K * Q.pt * 8 + (((size_t)Q.K * 4 + 15) & ~(size_t)15);
+        if (sums_b > (size_t)smem_max) return cudaSuccess;
+    }
+    *used = true;
+    cudaError_t e = cudaSuccess;
+    switch (NP) {
+        case 1: e = launch_rc_np<1>(P, warps, smem, s); break;
+        case 2: e = launch_rc_np<2>(P, warps, smem, s); break;
+        case 3: e = launch_rc_np<3>(P, warps, smem, s); break;
+        case 4: e = launch_rc_np<4>(P, warps, smem, s); break;
+        case 5: e = launch_rc_np<5>(P, warps, smem, s); break;
+        case 6: e = launch_rc_np<6>(P, warps, smem, s); break;
+        case 7: e = launch_rc_np<7>(P, warps, smem, s); break;
+        case 8: e = launch_rc_np<8>(P, warps, smem, s); break;
+        case 9: e = launch_rc_np<9>(P, warps, smem, s); break;
+        case 10: e = launch_rc_np<10>(P, warps, smem, s); break;
+        case 11: e = launch_rc_np<11>(P, warps, smem, s); break;
+        case 12: e = launch_rc_np<12>(P, warps, smem, s); break;
+        case 13: e = launch_rc_np<13>(P, warps, smem, s); break;
+        case 14: e = launch_rc_np<14>(P, warps, smem, s); break;
+        case 15: e = launch_rc_np<15>(P, warps, smem, s); break;
+        default: e = launch_rc_np<16>(P, warps, smem, s); break;
+    }
+    if (e != cudaSuccess || Q.do_update != 1) return e;
+    bool sums_used = false;
+    return launch_sums(Q, s, &sums_used);
+}
+
 }  // namespace
 
 static cudaError_t launch_kmeans_mode(const sk_ctx &c, const int32_t *idx, const float *val,
@@ -629,6 +1086,9 @@ static cudaError_t launch_kmeans_mode(const sk_ctx &c, const int32_t *idx, const
     P.changed = reinterpret_cast<unsigned long long *>(changed);
     P.mode = mode;
     P.expect = expect;
+    bool used = false;
+    const cudaError_t e = launch_rc(P, s, &used);
+    if (used || e != cudaSuccess) return e;
     if (K <= 64) return launch_kpl<2>(P, s);
     if (K <= 128) return launch_kpl<4>(P, s);
     return launch_kpl<8>(P, s);
