@@ -620,11 +620,12 @@ __device__ __forceinline__ uint64_t lds64(uint32_t addr) {
 }
 
 // Threads per CTA of the rotated-copies pass: up to 32 warps while a lane's
-// NP accumulator pairs and offsets fit 64 registers, 20 warps above that.
+// NP accumulator pairs and offsets fit 64 registers, then 24, 20 and 16 warps
+// as NP grows (no register spills).
 // (A row whose distances are all NaN keeps the label 0x7fffffff, which every
 // update skips.)
 template <int NP>
-constexpr int rc_max_threads() { return NP <= 9 ? 1024 : 640; }
+constexpr int rc_max_threads() { return NP <= 6 ? 1024 : NP <= 9 ? 768 : NP <= 12 ? 640 : 512; }
 
 template <int NP>
 __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParams P) {
