@@ -22,6 +22,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                      average equals C_emp (unbiasedness, Sec. V / Appendix C);
                      m = p reduces to (1/n) Y^T Y exactly
   sample_mean     -- exhaustive enumeration: unbiased (Sec. IV)
+  cov_centred     -- exhaustive enumeration over every pair of masks of two
+                     rows at p = 8: the mask average equals the centred second
+                     moment (1/n) Y^T Y - ybar ybar^T; m = p reduces to it
+                     exactly
   kmeans          -- m = p reduces to Lloyd's on H D X (Sec. VI-A), brute-force
                      argmin on tiny inputs, J' non-increasing (Sec. VI-B)
   unmix           -- D H (H D x) = x; back-map (HD)^T C_emp(Y) (HD) = C_emp(X)
@@ -94,6 +98,7 @@ def _load():
             "oracle_gram": (None, [vp, vp, i64, i64, i64, vp]),
             "oracle_cov_finalize": (None, [vp, i64, i64, i64, vp]),
             "oracle_sample_mean": (None, [vp, vp, i64, i64, i64, vp]),
+            "oracle_cov_centred": (None, [vp, vp, i64, i64, i64, vp]),
             "oracle_kmeans_assign": (None, [vp, vp, i64, i64, vp, i64, i64, vp, vp]),
             "oracle_kmeans_update": (None, [vp, vp, vp, i64, i64, i64, i64, vp, vp, vp, vp]),
             "oracle_unmix": (None, [vp, i64, i64, i64, u64, vp]),
@@ -228,6 +233,18 @@ def cov_finalize(G, n: int, m: int) -> np.ndarray:
 def cov(idx, val, pt: int) -> np.ndarray:
     idx = np.asarray(idx)
     return cov_finalize(gram(idx, val, pt), idx.shape[0], idx.shape[1])
+
+
+def cov_centred(G, mean, n: int, m: int) -> np.ndarray:
+    """Centred covariance estimate C_n - xbar xbar^T + B(C_n)/n from the Gram
+    of n rows and their sample-mean estimate xbar (unbiased for the centred
+    second moment; derivation in sk_oracle.c)."""
+    G = _c(G, np.float64)
+    mean = _c(mean, np.float64)
+    pt = G.shape[0]
+    C = np.zeros_like(G)
+    _load().oracle_cov_centred(_p(G), _p(mean), n, m, pt, _p(C))
+    return C
 
 
 def sample_mean(idx, val, pt: int) -> np.ndarray:

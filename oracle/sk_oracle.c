@@ -265,6 +265,32 @@ void oracle_cov_finalize(const double *G, int64_t n, int64_t m, int64_t pt, doub
     for (int64_t j = 0; j < pt; ++j) C[j * pt + j] -= corr * C[j * pt + j];
 }
 
+/* Centred covariance estimate, built from the paper's two estimators: with
+ * C_n the covariance estimate above (Sec. V) and xbar the sample-mean estimate
+ * (Sec. IV) of the same n rows,
+ *   C_c = C_n - xbar xbar^T + (1/n) B(C_n),
+ *   B(A)_jj = ((P - m)/m) A_jj,  B(A)_jk = -((P - m)/(m (P - 1))) A_jk (j != k).
+ * B(C_emp)/n is the covariance of xbar over the masks: by Thm. B1 a mask keeps
+ * j with probability m/P and the pair (j, k) with m(m-1)/(P(P-1)), so
+ * Cov((P/m) R R^T y) has diagonal (P/m - 1) y_j^2 and off-diagonal
+ * (P(m-1)/(m(P-1)) - 1) y_j y_k; summed over independent rows and divided by
+ * n^2 that is B(C_emp)/n.  Hence E[xbar xbar^T] = ybar ybar^T + B(C_emp)/n,
+ * and since E[C_n] = C_emp and B is linear, E[C_c] = C_emp - ybar ybar^T, the
+ * centred second moment.  mean: xbar (length pt); C: pt x pt output. */
+void oracle_cov_centred(const double *G, const double *mean, int64_t n, int64_t m, int64_t pt,
+                        double *C) {
+    oracle_cov_finalize(G, n, m, pt, C);
+    double P = (double)pt, M = (double)m, N = (double)n;
+    double dcoef = (P - M) / M / N;
+    double ocoef = -(P - M) / (M * (P - 1.0)) / N;
+    for (int64_t j = 0; j < pt; ++j)
+        for (int64_t k = 0; k < pt; ++k) {
+            double cn = C[j * pt + k];
+            double b = (j == k ? dcoef : ocoef) * cn;
+            C[j * pt + k] = cn + b - mean[j] * mean[k];
+        }
+}
+
 /* Sample-mean estimator (Sec. IV, Thm. "sampleMean"): (pt/m)(1/n) sum_i w_i. */
 void oracle_sample_mean(const int32_t *idx, const double *val, int64_t n, int64_t m,
                         int64_t pt, double *mean) {

@@ -123,3 +123,66 @@ def test_sampling_matrix_moments_by_enumeration():
     expect = M * (M - 1) / (P * (P - 1)) * np.outer(x, x) + \
         M * (P - M) / (P * (P - 1)) * np.diag(x * x)
     assert np.max(np.abs(acc - expect)) < 1e-14
+
+
+@pytest.mark.parametrize("m", [2, 3, 5])
+def test_cov_centred_unbiased_by_enumeration(m):
+    """The centred estimate C_n - xbar xbar^T + B(C_n)/n, averaged over every
+    pair of masks of two rows (independent masks per row, Sec. I-A), equals
+    the centred second moment (1/n) Y^T Y - ybar ybar^T of the rows.
+    Without the correction B the average would be off by the covariance of
+    xbar; a wrong sign or a swapped diagonal/off-diagonal term fails here."""
+    pt, n = 8, 2
+    rng = np.random.default_rng(40 + m)
+    Y = rng.standard_normal((n, pt)) + 0.7
+    masks = _all_masks(pt, m)
+    acc = np.zeros((pt, pt))
+    for om0 in masks:
+        for om1 in masks:
+            idx = np.array([om0, om1], np.int32)
+            val = np.take_along_axis(Y, idx, axis=1)
+            G = oracle.gram(idx, val, pt)
+            mean = oracle.sample_mean(idx, val, pt)
+            acc += oracle.cov_centred(G, mean, n, m)
+    acc /= len(masks) ** 2
+    ybar = Y.mean(axis=0)
+    expect = Y.T @ Y / n - np.outer(ybar, ybar)
+    assert np.max(np.abs(acc - expect)) < 1e-13
+
+
+def test_cov_centred_full_sampling_is_plain_centred_gram():
+    """m = p: every row is kept whole, the correction vanishes and the
+    estimate is the centred second moment itself."""
+    pt, n = 16, 30
+    rng = np.random.default_rng(12)
+    Y = rng.standard_normal((n, pt)) - 1.5
+    idx = np.stack([rng.permutation(pt) for _ in range(n)]).astype(np.int32)
+    val = np.take_along_axis(Y, idx, axis=1)
+    C = oracle.cov_centred(oracle.gram(idx, val, pt), oracle.sample_mean(idx, val, pt), n, pt)
+    ybar = Y.mean(axis=0)
+    assert np.max(np.abs(C - (Y.T @ Y / n - np.outer(ybar, ybar)))) < 1e-13
+
+
+def test_cov_centred_needs_its_correction():
+    """The plain plug-in C_n - xbar xbar^T is biased: its mask average misses
+    the centred second moment by the covariance of xbar, B(C_emp)/n, which the
+    correction term of the centred estimate removes (checked at p = 8)."""
+    pt, n, m = 8, 2, 3
+    rng = np.random.default_rng(77)
+    Y = rng.standard_normal((n, pt)) + 0.3
+    masks = _all_masks(pt, m)
+    acc = np.zeros((pt, pt))
+    for om0 in masks:
+        for om1 in masks:
+            idx = np.array([om0, om1], np.int32)
+            val = np.take_along_axis(Y, idx, axis=1)
+            xbar = oracle.sample_mean(idx, val, pt)
+            acc += oracle.cov(idx, val, pt) - np.outer(xbar, xbar)
+    acc /= len(masks) ** 2
+    ybar = Y.mean(axis=0)
+    target = Y.T @ Y / n - np.outer(ybar, ybar)
+    Ce = Y.T @ Y / n
+    P, M = float(pt), float(m)
+    B = (P - M) / M * (np.diag(np.diag(Ce)) - (Ce - np.diag(np.diag(Ce))) / (P - 1))
+    assert np.max(np.abs(acc - target)) > 1e-2
+    assert np.max(np.abs(acc - (target - B / n))) < 1e-13
