@@ -31,6 +31,13 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
   unmix           -- D H (H D x) = x; back-map (HD)^T C_emp(Y) (HD) = C_emp(X)
   pca_topk        -- LAPACK eigh (library); compared as subspaces
   compress_raw    -- val = x[idx] with the (pinned) mask; raw padding is zero
+  dct, idct       -- scipy.fft's orthonormal DCT-II / DCT-III (library);
+                     orthonormality; closed forms (constant vector, cosine
+                     basis vectors); entries bounded by sqrt(2/p), the
+                     coherence behind eta = 1/2 of Sec. III, and the tail
+                     bound 2 exp(-t^2/4) over random signs
+  precondition/compress/unmix with dct -- the same pins as the Hadamard
+                     forms with p in place of pt (no padding)
   kmeans_2pass    -- brute-force dense distances and per-label means on small
                      inputs; converged Lloyd's is a fixed point (Algorithm 2)
   kmeans_hk       -- m = pt gives H_k = I exactly; ||H_k - I|| within the
@@ -107,6 +114,11 @@ def _load():
             "oracle_kpp_draw": (u64, [u64, u32, u32, u64]),
             "oracle_kmeanspp": (None, [vp, vp, i64, i64, i64, i64, u64, u32, vp, vp]),
             "oracle_kmeans_hk": (None, [vp, vp, i64, i64, i64, vp]),
+            "oracle_dct2": (None, [vp, i64]),
+            "oracle_dct3": (None, [vp, i64]),
+            "oracle_precondition_dct": (None, [vp, i64, i64, i64, u64, vp]),
+            "oracle_compress_dct": (None, [vp, i64, i64, i64, i64, i64, u64, vp, vp]),
+            "oracle_unmix_dct": (None, [vp, i64, i64, u64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -177,23 +189,44 @@ def fwht(y) -> np.ndarray:
     return a
 
 
-def precondition(X, seed: int) -> np.ndarray:
-    """Y = H D [X, 0] row by row (n x pt), from float32 samples."""
+def dct(y) -> np.ndarray:
+    """Orthonormal DCT-II of a vector (the direct sum, Sec. III's DCT H)."""
+    a = _c(y, np.float64).copy()
+    _load().oracle_dct2(_p(a), a.size)
+    return a
+
+
+def idct(y) -> np.ndarray:
+    """Its transpose, the orthonormal DCT-III (the inverse)."""
+    a = _c(y, np.float64).copy()
+    _load().oracle_dct3(_p(a), a.size)
+    return a
+
+
+def precondition(X, seed: int, dct: bool = False) -> np.ndarray:
+    """Y = H D [X, 0] row by row (n x pt), from float32 samples; with dct the
+    DCT of length p (no padding, n x p)."""
     X = _c(X, np.float32)
     n, p = X.shape
+    if dct:
+        Y = np.zeros((n, p), np.float64)
+        _load().oracle_precondition_dct(_p(X), n, p, p, seed, _p(Y))
+        return Y
     pt = ptilde(p)
     Y = np.zeros((n, pt), np.float64)
     _load().oracle_precondition(_p(X), n, p, p, seed, _p(Y))
     return Y
 
 
-def compress(X, m: int, seed: int, row0: int = 0):
-    """ELL form (idx int32 n x m, val float64 n x m) of rows row0.. of X."""
+def compress(X, m: int, seed: int, row0: int = 0, dct: bool = False):
+    """ELL form (idx int32 n x m, val float64 n x m) of rows row0.. of X; with
+    dct the DCT preconditioner and masks over [0, p)."""
     X = _c(X, np.float32)
     n, p = X.shape
     idx = np.zeros((n, m), np.int32)
     val = np.zeros((n, m), np.float64)
-    _load().oracle_compress(_p(X), n, p, p, row0, m, seed, _p(idx), _p(val))
+    fn = _load().oracle_compress_dct if dct else _load().oracle_compress
+    fn(_p(X), n, p, p, row0, m, seed, _p(idx), _p(val))
     return idx, val
 
 
@@ -361,10 +394,14 @@ def kmeans_hk(counts, nk, pt: int, m: int) -> np.ndarray:
     return dev
 
 
-def unmix(M, p: int, seed: int) -> np.ndarray:
-    """mu = D H mu' truncated to p coordinates, row by row (Eq. (mu-mu'))."""
+def unmix(M, p: int, seed: int, dct: bool = False) -> np.ndarray:
+    """mu = D H^T mu' truncated to p coordinates, row by row (Eq. (mu-mu'));
+    with dct, H is the DCT and mu' has p coordinates."""
     M = _c(M, np.float64)
     r, pt = M.shape
     out = np.zeros((r, p), np.float64)
-    _load().oracle_unmix(_p(M), r, pt, p, seed, _p(out))
+    if dct:
+        _load().oracle_unmix_dct(_p(M), r, p, seed, _p(out))
+    else:
+        _load().oracle_unmix(_p(M), r, pt, p, seed, _p(out))
     return out

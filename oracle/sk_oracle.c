@@ -351,6 +351,87 @@ void oracle_kmeans_update(const int32_t *idx, const double *val, const int32_t *
 
 /* Eq. (mu-mu'): mu = (HD)^T mu' = D H mu' (Sylvester H is symmetric),
  * truncated to the first p coordinates.  in is r x pt, out is r x p. */
+/* ---------------- DCT preconditioner (Sec. III: H a DCT matrix) ----------------
+ *
+ * H is the orthonormal DCT-II of length p (no padding: the sampling and the
+ * estimators then use p itself):
+ *   (H x)_k = s_k sum_{l=0}^{p-1} x_l cos(pi (2l + 1) k / (2p)),
+ *   s_0 = sqrt(1/p), s_k = sqrt(2/p) for k >= 1,
+ * written out as the direct O(p^2) sum.  Its transpose (the orthonormal
+ * DCT-III) is the un-mixing map.  The cosine's argument is reduced exactly in
+ * integers, (2l + 1) k mod 4p, before the one floating-point division. */
+static double dct_cos(int64_t a, int64_t p) {
+    const double pi = 3.14159265358979323846;
+    return cos(pi * (double)(a % (4 * p)) / (2.0 * (double)p));
+}
+
+void oracle_dct2(double *y, int64_t p) {
+    double *t = (double *)malloc((size_t)p * sizeof(double));
+    for (int64_t k = 0; k < p; ++k) {
+        double acc = 0.0;
+        for (int64_t l = 0; l < p; ++l) acc += y[l] * dct_cos((2 * l + 1) * k, p);
+        t[k] = (k == 0 ? sqrt(1.0 / (double)p) : sqrt(2.0 / (double)p)) * acc;
+    }
+    memcpy(y, t, (size_t)p * sizeof(double));
+    free(t);
+}
+
+void oracle_dct3(double *y, int64_t p) {
+    double *t = (double *)malloc((size_t)p * sizeof(double));
+    for (int64_t l = 0; l < p; ++l) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < p; ++k)
+            acc += (k == 0 ? sqrt(1.0 / (double)p) : sqrt(2.0 / (double)p)) * y[k] *
+                   dct_cos((2 * l + 1) * k, p);
+        t[l] = acc;
+    }
+    memcpy(y, t, (size_t)p * sizeof(double));
+    free(t);
+}
+
+/* y = H D x with the DCT H (Eq. (ROS)), row by row: Y is n x p. */
+void oracle_precondition_dct(const float *X, int64_t n, int64_t p, int64_t ldx, uint64_t seed,
+                             double *Y) {
+    double *D = (double *)malloc((size_t)p * sizeof(double));
+    oracle_signs(p, seed, D);
+    for (int64_t i = 0; i < n; ++i) {
+        double *y = Y + i * p;
+        for (int64_t j = 0; j < p; ++j) y[j] = D[j] * (double)X[i * ldx + j];
+        oracle_dct2(y, p);
+    }
+    free(D);
+}
+
+/* ELL form with the DCT preconditioner: the mask of global row r is the
+ * written spec's partial Fisher-Yates over [0, p). */
+void oracle_compress_dct(const float *X, int64_t n, int64_t p, int64_t ldx, int64_t row0,
+                         int64_t m, uint64_t seed, int32_t *idx, double *val) {
+    double *y = (double *)malloc((size_t)p * sizeof(double));
+    double *D = (double *)malloc((size_t)p * sizeof(double));
+    oracle_signs(p, seed, D);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < p; ++j) y[j] = D[j] * (double)X[i * ldx + j];
+        oracle_dct2(y, p);
+        oracle_mask(p, m, seed, row0 + i, idx + i * m);
+        for (int64_t t = 0; t < m; ++t) val[i * m + t] = y[idx[i * m + t]];
+    }
+    free(D);
+    free(y);
+}
+
+/* Un-mixing with the DCT: out_i = D H^T in_i (in, out: r x p). */
+void oracle_unmix_dct(const double *in, int64_t r, int64_t p, uint64_t seed, double *out) {
+    double *D = (double *)malloc((size_t)p * sizeof(double));
+    oracle_signs(p, seed, D);
+    for (int64_t i = 0; i < r; ++i) {
+        double *o = out + i * p;
+        memcpy(o, in + i * p, (size_t)p * sizeof(double));
+        oracle_dct3(o, p);
+        for (int64_t j = 0; j < p; ++j) o[j] *= D[j];
+    }
+    free(D);
+}
+
 void oracle_unmix(const double *in, int64_t r, int64_t pt, int64_t p, uint64_t seed,
                   double *out) {
     double *D = (double *)malloc((size_t)pt * sizeof(double));
