@@ -9,6 +9,7 @@
  *  - pt ("p tilde") is the smallest power of two >= p.  Samples are
  *    zero-padded to pt before the Walsh-Hadamard transform; all sampling
  *    and rescaling uses pt in place of the paper's p.  Supported: 1 <= p <= 8192.
+ *    With SK_FLAG_DCT (sk_init_ex) pt = p: the DCT needs no padding.
  *  - Every pointer argument named as device memory must be device memory the
  *    caller owns (for example torch storage); the library never frees it and
  *    keeps no reference to it after the call returns.  Host pointers are
@@ -65,7 +66,17 @@ enum {
      * comparison of Sec. VII): sk_compress samples the zero-padded raw row,
      * val = [x_i; 0][Omega], sk_precondition pads only, and sk_unmix /
      * sk_unmix_f64 truncate to p.  Estimators and K-means are unchanged. */
-    SK_FLAG_NO_PRECONDITION = 1
+    SK_FLAG_NO_PRECONDITION = 1,
+    /* The DCT preconditioner (Sec. III: H a DCT matrix; the paper's choice
+     * for p that is not a power of two, used in its Sec. VII big-data runs):
+     * H is the orthonormal DCT-II of length p, with no zero padding, so
+     * pt = p and the masks, the estimators' rescaling and every pt-sized
+     * buffer use p.  sk_unmix / sk_unmix_f64 apply D H^T (the DCT-III).
+     * Requires an even p whose half has no prime factor above 13 (for
+     * example 784 = 2 * 392 = 2 * 8 * 7 * 7, or 1000); otherwise
+     * SK_EUNSUPPORTED.  Excludes SK_FLAG_NO_PRECONDITION; not accepted by
+     * sk_batch_create (SK_EUNSUPPORTED). */
+    SK_FLAG_DCT = 2
 };
 
 /* Opaque host-side handle: p, pt, m, the seed and the flags.  Holds no
@@ -139,6 +150,20 @@ sk_status sk_cov_reset(const sk_ctx *ctx, double *G, void *stream);
  * G and C must not overlap. */
 sk_status sk_cov_finalize(const sk_ctx *ctx, const double *G, int64_t n_total,
                           double *C, void *stream);
+
+/* Centred covariance estimate: the uncentred C_n of Sec. V combined with the
+ * sample-mean estimate xbar of Sec. IV (sk_mean_finalize of the same rows),
+ *   C_c = C_n - xbar xbar^T + B(C_n) / n_total,
+ *   B(A)_jj = ((P-m)/m) A_jj,  B(A)_jk = -((P-m)/(m (P-1))) A_jk (j != k),
+ * with P = pt.  B(C_emp)/n is the covariance of xbar over the masks (from the
+ * keep probabilities m/P and m(m-1)/(P(P-1)) of Thm. B1), so the correction
+ * makes C_c unbiased for the centred second moment C_emp - ybar ybar^T (the
+ * plain plug-in C_n - xbar xbar^T is not).  G: the Gram accumulator of the
+ * n_total rows (upper triangle read, as sk_cov_finalize); mean: device float64
+ * pt; C: device float64 pt x pt (full symmetric), overlapping neither.
+ * Requires m >= 2 and n_total >= 1. */
+sk_status sk_cov_finalize_centred(const sk_ctx *ctx, const double *G, const double *mean,
+                                  int64_t n_total, double *C, void *stream);
 
 /* Top-k principal subspace of the symmetric pt x pt estimate C (device
  * float64), Sec. V PCA: eigenvalues (device float64, k, descending) and

@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sk.h")
 SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EUNSUPPORTED = range(6)
 SK_GRAM_FP32, SK_GRAM_BF16, SK_GRAM_BF16X3 = 0, 1, 2
 SK_FLAG_NO_PRECONDITION = 1
+SK_FLAG_DCT = 2
 STATUS_NAMES = {0: "SK_OK", 1: "SK_EINVAL", 2: "SK_ENOMEM", 3: "SK_ECUDA",
                 4: "SK_ETIMEOUT", 5: "SK_EUNSUPPORTED"}
 
@@ -59,6 +60,7 @@ def load(path: str | None = None):
             "sk_cov_workspace_bytes": (i64, [vp, ctypes.c_int, i64]),
             "sk_cov_finalize": (st, [vp, vp, i64, vp, vp]),
             "sk_cov_reset": (st, [vp, vp, vp]),
+            "sk_cov_finalize_centred": (st, [vp, vp, vp, i64, vp, vp]),
             "sk_kmeans_reset": (st, [vp, i32, vp, vp, vp, vp]),
             "sk_cov_topk": (st, [vp, vp, i32, i32, vp, vp, vp, vp]),
             "sk_cov_topk_workspace": (i64, [i64, i32]),
@@ -259,6 +261,19 @@ def sk_cov_finalize(ctx: Ctx, G, n_total: int, C=None, stream=None):
     _need(C, torch.float64, "C", (ctx.pt, ctx.pt))
     _check("sk_cov_finalize", load().sk_cov_finalize(ctx.handle, _ptr(G), int(n_total), _ptr(C),
                                                      _stream(stream)))
+    return C
+
+
+def sk_cov_finalize_centred(ctx: Ctx, G, mean, n_total: int, C=None, stream=None):
+    """Centred estimate C_n - xbar xbar^T + B(C_n)/n from G and the sample mean."""
+    _need(G, torch.float64, "G", (ctx.pt, ctx.pt))
+    _need(mean, torch.float64, "mean", (ctx.pt,))
+    if C is None:
+        C = torch.empty_like(G)
+    _need(C, torch.float64, "C", (ctx.pt, ctx.pt))
+    _check("sk_cov_finalize_centred",
+           load().sk_cov_finalize_centred(ctx.handle, _ptr(G), _ptr(mean), int(n_total), _ptr(C),
+                                          _stream(stream)))
     return C
 
 

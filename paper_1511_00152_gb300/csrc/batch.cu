@@ -121,6 +121,9 @@ sk_status sk_batch_create(sk_batch **b, const sk_batch_item *items, int32_t nd,
         if (pt < 256)
             return bfail(SK_EUNSUPPORTED, "sk_batch_create: item %d: pt = %lld < 256", d,
                          (long long)pt);
+        if (it.flags & SK_FLAG_DCT)
+            return bfail(SK_EUNSUPPORTED,
+                         "sk_batch_create: item %d: the DCT preconditioner is not batched", d);
         if (it.flags & ~(uint32_t)SK_FLAG_NO_PRECONDITION)
             return bfail(SK_EINVAL, "sk_batch_create: item %d: unknown flags", d);
         if (it.n < 0 || it.ldx < it.p || it.row0 < 0)

@@ -44,6 +44,7 @@ struct CompressParams {
     unsigned int *err;  // device error word (bounded waits)
     int ctas_per_sm;    // autotuned residency cap (0: as many as fit)
     long long wait_cycles;  // limit of each bounded mbarrier wait (SM clock cycles)
+    int mask_pt;        // range of the masks: pt (2^L, or p with the DCT)
 };
 
 constexpr int kNB = 2;  // staging buffers per warp (one unit in flight ahead)
@@ -230,7 +231,8 @@ template <int L, bool GATHER = true>
 __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
                                            const float *ybuf, int ebase, uint32_t *A,
                                            uint32_t *hit, uint32_t *words, uint32_t tag, int lane) {
-    constexpr int PT = 1 << L;
+    // the range [0, PT) of the draw: 2^L, or (masks alone) p <= 2^L for the DCT
+    const int PT = GATHER ? (1 << L) : P.mask_pt;
     const uint64_t g = (uint64_t)(P.row0 + i);
     const int m = P.m;
     int32_t *oidx = P.idx + i * (int64_t)m;
@@ -831,6 +833,7 @@ static CompressParams make_params(const sk_ctx &c, const float *X, int64_t n, in
     P.err = device_error_word();
     P.ctas_per_sm = c.compress_ctas;
     P.wait_cycles = wait_limit_cycles();
+    P.mask_pt = (int)c.pt;
     return P;
 }
 
@@ -910,11 +913,41 @@ cudaError_t compress_batch_launch(const CompressBatchInfo &info, unsigned char *
     return cudaGetLastError();
 }
 
+// Masks alone (mask_kernel) for any range pt <= 2^L.
+static cudaError_t launch_masks_any(int L, const CompressParams &P, cudaStream_t s) {
+    switch (L) {
+        case 0: return launch_masks<0>(P, s);
+        case 1: return launch_masks<1>(P, s);
+        case 2: return launch_masks<2>(P, s);
+        case 3: return launch_masks<3>(P, s);
+        case 4: return launch_masks<4>(P, s);
+        case 5: return launch_masks<5>(P, s);
+        case 6: return launch_masks<6>(P, s);
+        case 7: return launch_masks<7>(P, s);
+        case 8: return launch_masks<8>(P, s);
+        case 9: return launch_masks<9>(P, s);
+        case 10: return launch_masks<10>(P, s);
+        case 11: return launch_masks<11>(P, s);
+        case 12: return launch_masks<12>(P, s);
+        case 13: return launch_masks<13>(P, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
                             int64_t row0, int32_t *idx, float *val, float *Y,
                             cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const CompressParams P = make_params(c, X, n, ldx, row0, idx, val, Y);
+    if (c.flags & SK_FLAG_DCT) {
+        // the DCT preconditioner (no padding): masks over [0, p) first, then
+        // each row's transform and its gather (or the dense rows)
+        if (!Y) {
+            const cudaError_t e = launch_masks_any(c.log2pt, P, s);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_dct_forward(c, X, n, ldx, idx, val, Y, s);
+    }
     return Y ? dispatch<true>(c.log2pt, P, s) : dispatch<false>(c.log2pt, P, s);
 }
 

@@ -1,0 +1,406 @@
+// dct.cu -- the DCT preconditioner (Sec. III: y = H D x with H an orthonormal
+// DCT matrix; the preconditioner of the paper's big-data runs, Sec. VII) for
+// any even p without zero padding, and its transpose for un-mixing.
+//
+// The orthonormal DCT-II of length N = p is computed from one complex FFT of
+// length L = N / 2 (the even/odd reordering of J. Makhoul, "A fast cosine
+// transform in one and two dimensions", IEEE TASSP 1980):
+//   v_l = u_2l, v_{N-1-l} = u_{2l+1}; z_l = v_2l + i v_{2l+1};  Z = FFT_L(z);
+//   V_k = E_k + e^{-2 pi i k / N} O_k,  E_k = (Z_k + conj Z_{L-k}) / 2,
+//   O_k = (Z_k - conj Z_{L-k}) / (2i);  W_k = e^{-i pi k / (2N)} V_k;
+//   X_k = Re W_k,  X_{N-k} = -Im W_k  (0 < k < L),  y_k = s_k X_k,
+// s_0 = sqrt(1/N), s_k = sqrt(2/N).  The inverse (DCT-III, the un-mixing map
+// D H^T) runs the same steps backwards with the inverse FFT.
+// The FFT is a mixed-radix self-sorting (Stockham) transform in shared memory
+// (Govindaraju et al., "High performance discrete Fourier transforms on
+// graphics processors", SC'08): each stage of radix R takes the L / R
+// butterflies j, multiplies input r by the twiddle exp(-2 pi i k r / (Ns R))
+// (k = j mod Ns, Ns the product of the earlier radices), takes the R-point
+// DFT and writes output q to (j / Ns) Ns R + k + q Ns.  Supported radices are
+// 2, 3, 4, 5, 7, 8, 11, 13 (the factorisation of L is made at sk_init_ex).
+//
+// Forward rows (compress and precondition) are the hot path: one CTA per row
+// at a time, persistent over rows, with the FFT twiddles and the two
+// post-processing phase tables computed once per CTA in float32; the mask of
+// each row has already been drawn (mask_kernel, range p) and the CTA gathers
+// val = y[idx].  Un-mixing (few rows) computes its twiddles as it goes, in
+// float32 or float64.
+#include <cstring>
+
+#include "sk_internal.cuh"
+
+namespace sk {
+namespace {
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<float> {
+    using type = float2;
+};
+template <>
+struct Cx<double> {
+    using type = double2;
+};
+
+template <typename C2>
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+    C2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C2>
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) {
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+template <typename C2>
+__device__ __forceinline__ C2 csub(C2 a, C2 b) {
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+template <typename C2>
+__device__ __forceinline__ C2 cconj(C2 a) {
+    a.y = -a.y;
+    return a;
+}
+
+// exp(sign * i pi x) in the arithmetic of T.
+__device__ __forceinline__ float2 expipi(float x, float sign) {
+    float s, c;
+    sincospif(x, &s, &c);
+    return make_float2(c, sign * s);
+}
+__device__ __forceinline__ double2 expipi(double x, double sign) {
+    double s, c;
+    sincospi(x, &s, &c);
+    return make_double2(c, sign * s);
+}
+
+struct DctParams {
+    const void *in;   // forward: X (float, n x ldx); inverse: rows (T, n x N)
+    int64_t n, ldx;
+    int N, L;         // transform length (= p) and FFT length N / 2
+    int nf;
+    int fac[16];      // radices of L, in stage order
+    uint32_t k0, k1;  // seed (sign spec)
+    const int32_t *idx;  // forward gather: masks (n x m)
+    float *val;          // forward gather: output (n x m)
+    void *out;           // forward dense: Y (float, n x N); inverse: rows (T, n x N)
+    int m;
+};
+
+// Twiddle exp(-2 pi i dir t / L): dir = 1 forward, -1 inverse; from the
+// CTA's table (forward only) or computed.
+template <typename T, bool TABLE>
+struct Twiddle {
+    using C2 = typename Cx<T>::type;
+    const C2 *tab;
+    int L;
+    T dir;
+    __device__ __forceinline__ C2 operator()(int t) const {
+        if constexpr (TABLE) {
+            return tab[t];
+        } else {
+            return expipi((T)(2 * t) / (T)L, -dir);
+        }
+    }
+};
+
+// One Stockham stage of radix R: in -> out (both L complex in shared memory).
+template <int R, typename C2, typename TW>
+__device__ __forceinline__ void fft_stage(const C2 *in, C2 *out, int L, int Ns, const TW &tw,
+                                          int tid, int nthr) {
+    const int S = L / R;
+    const int st = L / (Ns * R);  // twiddle stride: k r st < L
+    C2 rt[R];                     // the R-th roots of unity, rt[s] = w_R^s
+#pragma unroll
+    for (int s = 0; s < R; ++s) rt[s] = tw(s * S);
+    for (int j = tid; j < S; j += nthr) {
+        const int jq = j / Ns;
+        const int k = j - jq * Ns;
+        C2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = in[j + r * S];
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw(k * r * st));
+        const int base = jq * Ns * R + k;
+        if constexpr (R == 2) {
+            out[base] = cadd(x[0], x[1]);
+            out[base + Ns] = csub(x[0], x[1]);
+        } else if constexpr (R == 4) {
+            const C2 a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+            const C2 c = cadd(x[1], x[3]), d = csub(x[1], x[3]);
+            // d times w_4 = exp(-2 pi i dir / 4) = -i dir
+            C2 dm;
+            dm.x = d.y * tw.dir;
+            dm.y = -d.x * tw.dir;
+            out[base] = cadd(a, c);
+            out[base + 2 * Ns] = csub(a, c);
+            out[base + Ns] = cadd(b, dm);
+            out[base + 3 * Ns] = csub(b, dm);
+        } else {
+            // the R-point DFT, one output at a time: y_q = sum_r x_r w_R^(r q)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                C2 acc = x[0];
+#pragma unroll
+                for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(x[r], rt[(r * q) % R]));
+                out[base + q * Ns] = acc;
+            }
+        }
+    }
+}
+
+// FFT of a (L complex) using b as the other buffer; returns the buffer that
+// holds the result.  The CTA's threads take part; syncs between stages.
+template <typename C2, typename TW>
+__device__ C2 *fft(C2 *a, C2 *b, const DctParams &P, const TW &tw, int tid, int nthr) {
+    int Ns = 1;
+    for (int s = 0; s < P.nf; ++s) {
+        const int R = P.fac[s];
+        switch (R) {
+            case 2: fft_stage<2>(a, b, P.L, Ns, tw, tid, nthr); break;
+            case 3: fft_stage<3>(a, b, P.L, Ns, tw, tid, nthr); break;
+            case 4: fft_stage<4>(a, b, P.L, Ns, tw, tid, nthr); break;
+            case 5: fft_stage<5>(a, b, P.L, Ns, tw, tid, nthr); break;
+            case 7: fft_stage<7>(a, b, P.L, Ns, tw, tid, nthr); break;
+            case 8: fft_stage<8>(a, b, P.L, Ns, tw, tid, nthr); break;
+            case 11: fft_stage<11>(a, b, P.L, Ns, tw, tid, nthr); break;
+            default: fft_stage<13>(a, b, P.L, Ns, tw, tid, nthr); break;
+        }
+        __syncthreads();
+        C2 *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+__device__ __forceinline__ bool sign_neg(const uint32_t *sgn, int l) {
+    return (sgn[l >> 5] >> (l & 31)) & 1u;
+}
+
+// Forward rows.  DENSE: Y[i] = H D x_i; else val[i, t] = (H D x_i)[idx[i, t]].
+template <bool DENSE>
+__global__ void __launch_bounds__(512) dct_forward_kernel(DctParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = P.N, L = P.L;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    float2 *tw = reinterpret_cast<float2 *>(smem_raw);  // L: exp(-2 pi i t / L)
+    float2 *ph = tw + L;                                 // L + 1: exp(-i pi k / (2N))
+    float2 *om = ph + (L + 1);                           // L + 1: exp(-2 pi i k / N)
+    float2 *b0 = om + (L + 1);                           // L
+    float2 *b1 = b0 + L;                                 // L
+    uint32_t *sgn = reinterpret_cast<uint32_t *>(b1 + L);  // ceil(N / 32)
+    for (int t = tid; t < L; t += nthr) tw[t] = expipi((float)(2 * t) / (float)L, -1.f);
+    for (int k = tid; k <= L; k += nthr) {
+        ph[k] = expipi((float)k / (float)(2 * N), -1.f);
+        om[k] = expipi((float)(2 * k) / (float)N, -1.f);
+    }
+    for (int w = tid; w < (N + 31) / 32; w += nthr) {
+        // sign bits of coordinates 32 w .. 32 w + 31: word w mod 4 of block w / 4
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)(w >> 2), 0u, 0u, kTagSign), P.k0, P.k1);
+        sgn[w] = pick_word(o, (uint32_t)w & 3u);
+    }
+    __syncthreads();
+    const Twiddle<float, true> twf{tw, L, 1.f};
+    const float s0 = sqrtf(1.f / (float)N), s1 = sqrtf(2.f / (float)N);
+    const float *X = static_cast<const float *>(P.in);
+    for (int64_t i = blockIdx.x; i < P.n; i += gridDim.x) {
+        // u = D x in the reordered sequence v, read as the floats of z
+        float *zf = reinterpret_cast<float *>(b0);
+        const float *xr = X + i * P.ldx;
+        for (int l = tid; l < N; l += nthr) {
+            float u = __ldcs(xr + l);
+            if (sign_neg(sgn, l)) u = -u;
+            const int q = (l & 1) ? N - 1 - (l >> 1) : (l >> 1);
+            zf[q] = u;
+        }
+        __syncthreads();
+        float2 *Z = fft(b0, b1, P, twf, tid, nthr);
+        float *y = reinterpret_cast<float *>(Z == b0 ? b1 : b0);
+        for (int k = tid; k <= L; k += nthr) {
+            const float2 Zk = Z[k == L ? 0 : k];
+            const float2 Zc = cconj(Z[k == 0 ? 0 : L - k]);
+            const float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
+            // (Zk - Zc) / (2i)
+            const float2 O = make_float2(0.5f * (Zk.y - Zc.y), -0.5f * (Zk.x - Zc.x));
+            const float2 V = cadd(E, cmul(om[k], O));
+            const float2 W = cmul(ph[k], V);
+            if (k < N) y[k] = (k == 0 ? s0 : s1) * W.x;
+            if (k > 0 && k < L) y[N - k] = s1 * (-W.y);
+        }
+        __syncthreads();
+        if constexpr (DENSE) {
+            float *Y = static_cast<float *>(P.out) + i * N;
+            for (int k = tid; k < N; k += nthr) Y[k] = y[k];
+        } else {
+            const int32_t *gi = P.idx + i * P.m;
+            float *ov = P.val + i * P.m;
+            for (int t = tid; t < P.m; t += nthr) ov[t] = y[clamp_index(__ldcg(gi + t), N)];
+        }
+        __syncthreads();
+    }
+}
+
+// Un-mixing rows: out_i = D H^T in_i (the orthonormal DCT-III, then signs).
+template <typename T>
+__global__ void __launch_bounds__(512) dct_inverse_kernel(DctParams P) {
+    using C2 = typename Cx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = P.N, L = P.L;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    C2 *b0 = reinterpret_cast<C2 *>(smem_raw);
+    C2 *b1 = b0 + L;
+    C2 *V = b1 + L;  // L + 1
+    const Twiddle<T, false> twi{nullptr, L, (T)-1};  // inverse FFT: exp(+2 pi i t / L)
+    const T s0 = sqrt((T)1 / (T)N), s1 = sqrt((T)2 / (T)N);
+    const T *in = static_cast<const T *>(P.in);
+    T *out = static_cast<T *>(P.out);
+    for (int64_t i = blockIdx.x; i < P.n; i += gridDim.x) {
+        const T *yr = in + i * N;
+        // X_k = y_k / s_k; W_k = X_k - i X_{N-k} (X_N = 0); V_k = e^{i pi k / (2N)} W_k
+        for (int k = tid; k <= L; k += nthr) {
+            const T Xk = k < N ? yr[k] / (k == 0 ? s0 : s1) : (T)0;
+            const T Xn = (k > 0) ? yr[N - k] / s1 : (T)0;
+            C2 W;
+            W.x = Xk;
+            W.y = -Xn;
+            V[k] = cmul(expipi((T)k / (T)(2 * N), (T)1), W);
+        }
+        __syncthreads();
+        // Z_k = E_k + i O_k with E_k = (V_k + conj V_{L-k}) / 2 and
+        // O_k = (V_k - conj V_{L-k}) / (2 e^{-2 pi i k / N})
+        for (int k = tid; k < L; k += nthr) {
+            const C2 Vk = V[k], Vc = cconj(V[L - k]);
+            C2 E, D;
+            E.x = (T)0.5 * (Vk.x + Vc.x);
+            E.y = (T)0.5 * (Vk.y + Vc.y);
+            D.x = (T)0.5 * (Vk.x - Vc.x);
+            D.y = (T)0.5 * (Vk.y - Vc.y);
+            const C2 O = cmul(D, expipi((T)(2 * k) / (T)N, (T)1));  // divide by e^{-2 pi i k / N}
+            C2 Zk;
+            Zk.x = E.x - O.y;
+            Zk.y = E.y + O.x;
+            b0[k] = Zk;
+        }
+        __syncthreads();
+        C2 *z = fft(b0, b1, P, twi, tid, nthr);
+        // v_q = floats of z / L; x_2l = v_l, x_{2l+1} = v_{N-1-l}; then signs
+        const T *zf = reinterpret_cast<const T *>(z);
+        T *xo = out + i * N;
+        for (int l = tid; l < N; l += nthr) {
+            const int q = (l & 1) ? N - 1 - (l >> 1) : (l >> 1);
+            T x = zf[q] / (T)L;
+            const uint4 o = philox4x32_10(make_uint4((uint32_t)(l >> 7), 0u, 0u, kTagSign), P.k0, P.k1);
+            if ((pick_word(o, ((uint32_t)l >> 5) & 3u) >> (l & 31)) & 1u) x = -x;
+            xo[l] = x;
+        }
+        __syncthreads();
+    }
+}
+
+int dct_threads(int L) {
+    int t = (L / 8 + 31) / 32 * 32;
+    if (t < 64) t = 64;
+    if (t > 512) t = 512;
+    return t;
+}
+
+DctParams make_dct(const sk_ctx &c) {
+    DctParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.N = (int)c.p;
+    P.L = (int)(c.p / 2);
+    P.nf = c.dct_nf;
+    for (int s = 0; s < c.dct_nf; ++s) P.fac[s] = c.dct_fac[s];
+    P.k0 = (uint32_t)c.seed;
+    P.k1 = (uint32_t)(c.seed >> 32);
+    P.m = (int)c.m;
+    return P;
+}
+
+template <typename K>
+cudaError_t launch_rows(K kern, const DctParams &P, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = dct_threads(P.L);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)sms * per_sm;
+    if (blocks > P.n) blocks = P.n;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// The radices of L = p / 2 in stage order (8, 4, 2 first, then odd primes up
+// to 13); false if L has a prime factor above 13.
+bool dct_factor(int64_t L, int *fac, int *nf) {
+    int k = 0;
+    while (L > 1 && L % 8 == 0 && k < 16) {
+        fac[k++] = 8;
+        L /= 8;
+    }
+    while (L > 1 && L % 4 == 0 && k < 16) {
+        fac[k++] = 4;
+        L /= 4;
+    }
+    while (L > 1 && L % 2 == 0 && k < 16) {
+        fac[k++] = 2;
+        L /= 2;
+    }
+    for (int r : {3, 5, 7, 11, 13})
+        while (L > 1 && L % r == 0 && k < 16) {
+            fac[k++] = r;
+            L /= r;
+        }
+    *nf = k;
+    return L == 1;
+}
+
+size_t dct_forward_smem(const sk_ctx &c) {
+    const size_t L = (size_t)(c.p / 2);
+    return (L + 2 * (L + 1) + 2 * L) * sizeof(float2) + ((size_t)c.p + 31) / 32 * 4;
+}
+
+cudaError_t launch_dct_forward(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                               const int32_t *idx, float *val, float *Y, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    DctParams P = make_dct(c);
+    P.in = X;
+    P.n = n;
+    P.ldx = ldx;
+    P.idx = idx;
+    P.val = val;
+    P.out = Y;
+    const size_t smem = dct_forward_smem(c);
+    return Y ? launch_rows(dct_forward_kernel<true>, P, smem, s)
+             : launch_rows(dct_forward_kernel<false>, P, smem, s);
+}
+
+cudaError_t launch_dct_inverse(const sk_ctx &c, const void *in, int64_t r, void *out, bool f64,
+                               cudaStream_t s) {
+    if (r == 0) return cudaSuccess;
+    DctParams P = make_dct(c);
+    P.in = in;
+    P.n = r;
+    P.out = out;
+    const size_t L = (size_t)P.L;
+    const size_t smem = (3 * L + 1) * (f64 ? sizeof(double2) : sizeof(float2));
+    return f64 ? launch_rows(dct_inverse_kernel<double>, P, smem, s)
+               : launch_rows(dct_inverse_kernel<float>, P, smem, s);
+}
+
+}  // namespace sk

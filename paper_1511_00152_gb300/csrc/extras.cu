@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(512) mean_scatter_kernel(const int32_t *__rest
     const int64_t r1 = (r0 + kMeanRows < n) ? r0 + kMeanRows : n;
     const int64_t e1 = r1 * m;
     for (int64_t e = r0 * m + threadIdx.x; e < e1; e += blockDim.x)
-        atomicAdd(ssum + (__ldg(idx + e) & (pt - 1)), __ldg(val + e));
+        atomicAdd(ssum + clamp_index(__ldg(idx + e), pt), __ldg(val + e));
     __syncthreads();
     for (int e = threadIdx.x; e < pt; e += blockDim.x)
         if (ssum[e] != 0.f) atomicAdd(sums + e, (double)ssum[e]);

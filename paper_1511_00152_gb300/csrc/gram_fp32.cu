@@ -11,6 +11,9 @@
 //
 // cov_finalize applies the rescaling and the diagonal correction of C_n
 // (Sec. V): off-diagonal P(P-1)/(m(m-1)) G/n, diagonal times (1 - (P-m)/(P-1)).
+// The centred form (C_n - xbar xbar^T + B(C_n)/n, with xbar the sample-mean
+// estimate of Sec. IV) scales each C_n entry once more, by 1 + (P-m)/(m n) on
+// the diagonal and 1 - (P-m)/(m (P-1) n) off it, and subtracts xbar_j xbar_k.
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -111,22 +114,25 @@ __global__ void __launch_bounds__(kThreads) gram_fp32_kernel(GramParams P) {
     __syncthreads();
     for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
         const float x = tile[e];
-        if (x != 0.f) {
-            const int a = e / T, b = e - a * T;
+        const int a = e / T, b = e - a * T;
+        // the last block of a pt that is not a multiple of T is ragged
+        if (x != 0.f && bi * T + a < P.pt && bj * T + b < P.pt) {
             atomicAdd(P.G + (int64_t)(bi * T + a) * P.pt + (bj * T + b), (double)x);
         }
     }
 }
 
 __global__ void cov_finalize_kernel(const double *G, int pt, double scale_off,
-                                    double scale_diag, double *C) {
+                                    double scale_diag, double cen_off, double cen_diag,
+                                    const double *mean, double *C) {
     const int64_t total = (int64_t)pt * pt;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / pt), k = (int)(e - (int64_t)j * pt);
         const int a = j < k ? j : k, b = j < k ? k : j;
         const double g = G[(int64_t)a * pt + b];
-        C[e] = (j == k) ? g * scale_diag : g * scale_off;
+        const double cn = (j == k) ? g * scale_diag : g * scale_off;
+        C[e] = mean ? cn * ((j == k) ? cen_diag : cen_off) - mean[j] * mean[k] : cn;
     }
 }
 
@@ -141,10 +147,13 @@ cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *v
     P.n = n;
     P.m = (int)c.m;
     P.pt = (int)c.pt;
-    P.T = c.pt < 128 ? (int)c.pt : 128;
+    // tiles of T x T with T a power of two (the smallest >= pt below 128);
+    // the last block is ragged when pt is not a multiple of T
+    P.T = 128;
+    while (P.T > 1 && P.T / 2 >= c.pt) P.T /= 2;
     P.logT = 0;
     while ((1 << P.logT) < P.T) ++P.logT;
-    P.nb = (int)(c.pt / P.T);
+    P.nb = (int)((c.pt + P.T - 1) / P.T);
     P.cap = P.m < P.T ? P.m : P.T;
     P.G = G;
     const int ntiles = P.nb * (P.nb + 1) / 2;
@@ -168,14 +177,17 @@ cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *v
 }
 
 cudaError_t launch_cov_finalize(const sk_ctx &c, const double *G, int64_t n_total,
-                                double *C, cudaStream_t s) {
-    const double P = (double)c.pt, M = (double)c.m;
-    const double off = P * (P - 1.0) / (M * (M - 1.0)) / (double)n_total;
+                                const double *mean, double *C, cudaStream_t s) {
+    const double P = (double)c.pt, M = (double)c.m, N = (double)n_total;
+    const double off = P * (P - 1.0) / (M * (M - 1.0)) / N;
     const double diag = off * (1.0 - (P - M) / (P - 1.0));
+    const double cen_diag = 1.0 + (P - M) / M / N;
+    const double cen_off = 1.0 - (P - M) / (M * (P - 1.0)) / N;
     const int64_t total = c.pt * c.pt;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 8192) blocks = 8192;
-    cov_finalize_kernel<<<blocks, 256, 0, s>>>(G, (int)c.pt, off, diag, C);
+    cov_finalize_kernel<<<blocks, 256, 0, s>>>(G, (int)c.pt, off, diag, cen_off, cen_diag, mean,
+                                               C);
     return cudaGetLastError();
 }
 

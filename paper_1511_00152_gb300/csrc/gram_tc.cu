@@ -199,7 +199,7 @@ __device__ __forceinline__ void bucket_body(const int32_t *idx, const float *val
     __syncthreads();
     for (int e0 = 0; e0 < total; e0 += blockDim.x) {
         const int e = e0 + tid;
-        const int c = e < total ? ((__ldg(gi + e) & (pt - 1)) >> 7) : -1 - lane;
+        const int c = e < total ? (clamp_index(__ldg(gi + e), pt) >> 7) : -1 - lane;
         const unsigned grp = __match_any_sync(0xffffffffu, c);
         if (e < total && (grp & lt) == 0u) atomicAdd(&hist[c], __popc(grp));
     }
@@ -220,7 +220,7 @@ __device__ __forceinline__ void bucket_body(const int32_t *idx, const float *val
         int j = 0, c = -1 - lane;
         float v = 0.f;
         if (e < total) {
-            j = __ldg(gi + e) & (pt - 1);
+            j = clamp_index(__ldg(gi + e), pt);
             v = __ldg(gv + e);
             c = j >> 7;
         }
@@ -341,7 +341,8 @@ __device__ __forceinline__ void gram_tc_body(const TcParams &P, int bid) {
                 }
                 const int *o = P.boff + (slab0 + i) * nb1;
                 const int a0 = __ldg(o + bi), a1 = __ldg(o + bi + 1);
-                const int b0 = __ldg(o + bj * R), b1 = __ldg(o + bj * R + R);
+                const int bhi = bj * R + R < P.nblk ? bj * R + R : P.nblk;  // ragged last tile
+                const int b0 = __ldg(o + bj * R), b1 = __ldg(o + bhi);
                 const int64_t E0 = (slab0 + i) * (int64_t)kSlab * P.m;  // slab's first entry
                 // 16-byte aligned covers of the two ranges (entries are 8 bytes)
                 const int64_t sa = (E0 + a0) & ~int64_t(1), ea = (E0 + a1 + 1) & ~int64_t(1);
@@ -578,10 +579,13 @@ __device__ __forceinline__ void gram_tc_body(const TcParams &P, int bid) {
         }
         if (have && drained && !*abort_flag && has_cols) {
             const int row = I0 + q * 32 + lane;
-            double *g = P.G + (int64_t)row * P.pt + (J0 + hcol * 128);
+            const int col0 = J0 + hcol * 128;
+            if (row < P.pt) {
+                double *g = P.G + (int64_t)row * P.pt + col0;
 #pragma unroll
-            for (int j = 0; j < 128; ++j)
-                if (acc[j] != 0.f) atomicAdd(g + j, (double)acc[j]);
+                for (int j = 0; j < 128; ++j)
+                    if (acc[j] != 0.f && col0 + j < P.pt) atomicAdd(g + j, (double)acc[j]);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -615,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_batch_kernel(const TcPara
 int64_t gram_tc_workspace(const sk_ctx &c, int64_t n) {
     if (n <= 0) return 0;
     const int64_t nslab = (n + kSlab - 1) / kSlab;
-    const int64_t nblk = c.pt / kBlk;
+    const int64_t nblk = (c.pt + kBlk - 1) / kBlk;
     const int64_t ent = nslab * kSlab * c.m * (int64_t)sizeof(int2);
     const int64_t offs = nslab * (nblk + 1) * (int64_t)sizeof(int);
     return ((ent + 255) & ~int64_t(255)) + offs + 256;
@@ -632,10 +636,13 @@ static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const 
     P.n = n;
     P.m = (int)c.m;
     P.pt = (int)c.pt;
-    P.N = c.pt >= 256 ? 256 : (int)c.pt;
+    // column tiles of 256 (128 below pt = 256 or when autotuned); a pt that is
+    // not a multiple of the tile sizes leaves ragged last blocks whose extra
+    // rows and columns hold no entries
+    P.N = c.pt >= 256 ? 256 : 128;
     if (c.gram_n == 128 && c.pt >= 128) P.N = 128;  // autotuned tile width
-    P.nbi = P.pt / kTileM;
-    P.nbj = P.pt / P.N;
+    P.nbi = (P.pt + kTileM - 1) / kTileM;
+    P.nbj = (P.pt + P.N - 1) / P.N;
     const int ratio = P.N / kTileM;
     P.ntiles = 0;
     for (int bi = 0; bi < P.nbi; ++bi) P.ntiles += P.nbj - bi / ratio;
@@ -646,7 +653,7 @@ static cudaError_t tc_plan(const sk_ctx &c, int mode, const int32_t *idx, const 
     if (P.N == 128 && P.hilo) P.nstages = 3;
     P.G = G;
     P.wait_cycles = wait_limit_cycles();
-    P.nblk = P.pt / kBlk;
+    P.nblk = (P.pt + kBlk - 1) / kBlk;
     // workspace: bucketed entries (8 bytes each, 64 m per slab), then offsets
     nslab = (n + kSlab - 1) / kSlab;
     const int64_t ent = nslab * kSlab * c.m * (int64_t)sizeof(int2);

@@ -111,7 +111,6 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
     const int kbase = kl * KPL;
     int2 *stage = stage_all + (size_t)warp * P.stage_cap;
     const int m = P.m;
-    const int pmask = P.pt - 1;
 
     for (int64_t base = base0; base < r_end; base += step) {
         const int rows_here = (int)((r_end - base) < P.RW ? (r_end - base) : P.RW);
@@ -145,10 +144,10 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
                     float v;
                     if constexpr (STAGE) {
                         const int2 iv = rs[t];
-                        j = iv.x & pmask;  // indices outside [0, pt) wrap
+                        j = clamp_index(iv.x, P.pt);  // indices outside [0, pt) are clamped
                         v = __int_as_float(iv.y);
                     } else {
-                        j = __ldg(ri + t) & pmask;
+                        j = clamp_index(__ldg(ri + t), P.pt);
                         v = __ldg(rv + t);
                     }
                     const uint64_t vv = pack2(v, v);
@@ -231,10 +230,10 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
                         float v;
                         if constexpr (STAGE) {
                             const int2 iv = stage[rs * m + t];
-                            j = iv.x & pmask;
+                            j = clamp_index(iv.x, P.pt);
                             v = __int_as_float(iv.y);
                         } else {
-                            j = __ldg(P.idx + (base + rs) * m + t) & pmask;
+                            j = clamp_index(__ldg(P.idx + (base + rs) * m + t), P.pt);
                             v = __ldg(P.val + (base + rs) * m + t);
                         }
                         if (PRIV && P.do_update == 1) {
@@ -282,10 +281,10 @@ __device__ __forceinline__ void kmeans_rows(const KmParams &P, const float *mus,
                     float v;
                     if constexpr (STAGE) {
                         const int2 iv = stage[rs * m + t];
-                        j = iv.x & pmask;
+                        j = clamp_index(iv.x, P.pt);
                         v = __int_as_float(iv.y);
                     } else {
-                        j = __ldg(P.idx + ii * m + t) & pmask;
+                        j = clamp_index(__ldg(P.idx + ii * m + t), P.pt);
                         v = __ldg(P.val + ii * m + t);
                     }
                     const int64_t slot = (int64_t)lab * P.pt + j;
@@ -676,7 +675,6 @@ __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParam
         off[q] = smem_u32(tab) + 8u * (uint32_t)(c * NP + pi);
     }
     const int m = P.m, S = P.S;
-    const int pmask = P.pt - 1;
     int2 *stage = stage_all + (size_t)warp * RW * S;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -721,7 +719,7 @@ __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParam
 #pragma unroll 2
             for (int t = c; t < m; t += C) {
                 const int2 iv = rs[t];
-                const uint32_t jb = (uint32_t)(iv.x & pmask) << 7;
+                const uint32_t jb = (uint32_t)clamp_index(iv.x, P.pt) << 7;
                 const float v = __int_as_float(iv.y);
                 const uint64_t vv = pack2(v, v);
 #pragma unroll
@@ -778,7 +776,7 @@ __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParam
             // (its C lanes move their own entries)
             for (int t = c; t < m; t += C) {
                 const int2 iv = rs[t];
-                const int j = iv.x & pmask;
+                const int j = clamp_index(iv.x, P.pt);
                 const double v = (double)__int_as_float(iv.y);
                 atomicAdd(P.Ssum + (int64_t)label * P.pt + j, v);
                 atomicAdd(P.cnt + (int64_t)label * P.pt + j, 1);
@@ -856,7 +854,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_sums_kernel(SumParams P) {
     }
     for (int e = tid; e < P.K; e += blockDim.x) snk[e] = 0;
     __syncthreads();
-    const int m = P.m, pmask = P.pt - 1;
+    const int m = P.m;
     const int wpb = blockDim.x >> 5;
     const int64_t nchunks = (P.n + 31) / 32;
     for (int64_t ch = (int64_t)blockIdx.x * wpb + warp; ch < nchunks;
@@ -893,7 +891,7 @@ __global__ void __launch_bounds__(kThreads) kmeans_sums_kernel(SumParams P) {
                 const int r = e < total ? (m == 1 ? e : (int)__umulhi((uint32_t)e, P.minv)) : 0;
                 const int le = __shfl_sync(kFull, lab, r);
                 if (e < total && (unsigned)le < (unsigned)P.K) {
-                    const int slot = le * P.pt + (jx[u] & pmask);
+                    const int slot = le * P.pt + clamp_index(jx[u], P.pt);
                     atomicAdd(sS + slot, vx[u]);
                     atomicAdd(sC + slot, 1);
                 }

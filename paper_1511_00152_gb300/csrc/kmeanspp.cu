@@ -159,7 +159,7 @@ __global__ void kpp_centre_kernel(KppWs ws, const int32_t *idx, const float *val
     for (int j = threadIdx.x; j < pt; j += blockDim.x) cen[j] = 0.f;
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int t = 0; t < m; ++t) cen[idx[c * m + t] & (pt - 1)] = val[c * m + t];
+        for (int t = 0; t < m; ++t) cen[clamp_index(idx[c * m + t], pt)] = val[c * m + t];
 }
 
 __global__ void __launch_bounds__(kRows) kpp_dist_kernel(KppWs ws, const int32_t *idx,
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kRows) kpp_dist_kernel(KppWs ws, const int32_t
         if (tid < rows) {
             for (int t = 0; t < cw; ++t) {
                 const int2 e = st[tid * (kChunk + 1) + t];
-                const float diff = __int_as_float(e.y) - cs[e.x & (pt - 1)];
+                const float diff = __int_as_float(e.y) - cs[clamp_index(e.x, pt)];
                 d = fmaf(diff, diff, d);
             }
         }

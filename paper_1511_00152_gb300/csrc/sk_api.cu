@@ -70,17 +70,33 @@ sk_status sk_init_ex(sk_ctx **ctx, int64_t p, int64_t m, uint64_t seed, uint32_t
     if (p > 8192) return fail(SK_EUNSUPPORTED, "sk_init: p = %lld > 8192", (long long)p);
     int L = 0;
     while ((1LL << L) < p) ++L;
-    const int64_t pt = 1LL << L;
+    if (flags & ~(uint32_t)(SK_FLAG_NO_PRECONDITION | SK_FLAG_DCT))
+        return fail(SK_EINVAL, "sk_init: unknown flag bits 0x%x", flags);
+    const bool dct = (flags & SK_FLAG_DCT) != 0;
+    int fac[16] = {0}, nf = 0;
+    if (dct) {
+        if (flags & SK_FLAG_NO_PRECONDITION)
+            return fail(SK_EINVAL, "sk_init: SK_FLAG_DCT and SK_FLAG_NO_PRECONDITION exclude each other");
+        if (p % 2 != 0)
+            return fail(SK_EUNSUPPORTED, "sk_init: the DCT preconditioner needs an even p (p = %lld)",
+                        (long long)p);
+        if (!sk::dct_factor(p / 2, fac, &nf))
+            return fail(SK_EUNSUPPORTED,
+                        "sk_init: the DCT preconditioner needs p / 2 without prime factors above 13 "
+                        "(p = %lld)", (long long)p);
+    }
+    // the DCT keeps pt = p (no padding)
+    const int64_t pt = dct ? p : 1LL << L;
     if (m < 1 || m > pt)
         return fail(SK_EINVAL, "sk_init: m = %lld must be in [1, pt = %lld]", (long long)m,
                     (long long)pt);
-    if (flags & ~(uint32_t)SK_FLAG_NO_PRECONDITION)
-        return fail(SK_EINVAL, "sk_init: unknown flag bits 0x%x", flags);
     sk_ctx *c = new (std::nothrow) sk_ctx;
     if (!c) return fail(SK_ENOMEM, "sk_init: out of host memory");
     c->p = p;
     c->pt = pt;
     c->log2pt = L;
+    c->dct_nf = nf;
+    for (int k = 0; k < 16; ++k) c->dct_fac[k] = fac[k];
     c->m = m;
     c->seed = seed;
     c->flags = flags;
@@ -171,8 +187,22 @@ sk_status sk_cov_finalize(const sk_ctx *ctx, const double *G, int64_t n_total, d
     if (!G || !C) return fail(SK_EINVAL, "sk_cov_finalize: NULL buffer");
     const size_t bytes = (size_t)ctx->pt * ctx->pt * sizeof(double);
     if (overlaps(G, bytes, C, bytes)) return fail(SK_EINVAL, "sk_cov_finalize: G and C overlap");
-    return cuda_status(sk::launch_cov_finalize(*ctx, G, n_total, C, as_stream(stream)),
+    return cuda_status(sk::launch_cov_finalize(*ctx, G, n_total, nullptr, C, as_stream(stream)),
                        "sk_cov_finalize");
+}
+
+sk_status sk_cov_finalize_centred(const sk_ctx *ctx, const double *G, const double *mean,
+                                  int64_t n_total, double *C, void *stream) {
+    SK_CHECK_CTX(ctx);
+    if (ctx->m < 2) return fail(SK_EINVAL, "sk_cov_finalize_centred: needs m >= 2 (Thm. B1)");
+    if (n_total < 1) return fail(SK_EINVAL, "sk_cov_finalize_centred: n_total < 1");
+    if (!G || !mean || !C) return fail(SK_EINVAL, "sk_cov_finalize_centred: NULL buffer");
+    const size_t bytes = (size_t)ctx->pt * ctx->pt * sizeof(double);
+    const size_t mbytes = (size_t)ctx->pt * sizeof(double);
+    if (overlaps(G, bytes, C, bytes) || overlaps(mean, mbytes, C, bytes))
+        return fail(SK_EINVAL, "sk_cov_finalize_centred: C overlaps G or mean");
+    return cuda_status(sk::launch_cov_finalize(*ctx, G, n_total, mean, C, as_stream(stream)),
+                       "sk_cov_finalize_centred");
 }
 
 int64_t sk_cov_topk_workspace(int64_t pt, int32_t k) {

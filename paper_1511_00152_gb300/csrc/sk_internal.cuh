@@ -89,6 +89,14 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return y * pow2(-e);
 }
 
+// Index j of a caller's ELL entry kept inside [0, pt): the identity for
+// valid input (sk_compress writes indices below pt); a bad index is clamped
+// rather than reaching outside the library's arrays.  pt need not be a power
+// of two (the DCT preconditioner keeps pt = p).
+__device__ __forceinline__ int clamp_index(int j, int pt) {
+    return (int)min((unsigned)j, (unsigned)(pt - 1));
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -114,6 +122,10 @@ struct sk_ctx {
     int gram_n;      // Gram tile width, 128 or 256
     int split_mult;  // multiplier on the Gram row-split count
     int compress_ctas;  // compress CTAs per SM (1 or 2)
+    // SK_FLAG_DCT: radices of the FFT of length p / 2 (pt = p, no padding;
+    // log2pt is then the exponent of the next power of two, for sizing only)
+    int dct_nf;
+    int dct_fac[16];
 };
 
 namespace sk {
@@ -177,6 +189,16 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
 cudaError_t kmeans_batch_launch(const KmeansBatchInfo &info, unsigned char *dev_table, int op,
                                 cudaStream_t s);
 
+// The DCT preconditioner (dct.cu): factorisation of p / 2 at sk_init_ex; the
+// forward rows (Y != NULL: dense y = H D x; else val = y[idx] with the masks
+// already in idx) and the un-mixing rows D H^T (float32 or float64).
+bool dct_factor(int64_t L, int *fac, int *nf);
+size_t dct_forward_smem(const sk_ctx &c);
+cudaError_t launch_dct_forward(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
+                               const int32_t *idx, float *val, float *Y, cudaStream_t s);
+cudaError_t launch_dct_inverse(const sk_ctx &c, const void *in, int64_t r, void *out, bool f64,
+                               cudaStream_t s);
+
 cudaError_t launch_compress(const sk_ctx &c, const float *X, int64_t n, int64_t ldx,
                             int64_t row0, int32_t *idx, float *val, float *Y,
                             cudaStream_t s);
@@ -197,8 +219,9 @@ cudaError_t launch_gram_fp32(const sk_ctx &c, const int32_t *idx, const float *v
 cudaError_t launch_gram_tc(const sk_ctx &c, int mode, const int32_t *idx,
                            const float *val, int64_t n, double *G, void *work, cudaStream_t s);
 int64_t gram_tc_workspace(const sk_ctx &c, int64_t n);
+// mean == NULL: C_n; else the centred estimate with mean the sample-mean estimate
 cudaError_t launch_cov_finalize(const sk_ctx &c, const double *G, int64_t n_total,
-                                double *C, cudaStream_t s);
+                                const double *mean, double *C, cudaStream_t s);
 cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out,
                          bool f64, cudaStream_t s);
 // K-means++ seeding and the objective J' (kmeanspp.cu).

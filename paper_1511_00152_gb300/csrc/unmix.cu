@@ -38,6 +38,8 @@ __global__ void unmix_kernel(const T *in, int64_t r, int pt, int p, uint32_t k0,
 cudaError_t launch_unmix(const sk_ctx &c, const void *in, int64_t r, void *out, bool f64,
                          cudaStream_t s) {
     if (r == 0) return cudaSuccess;
+    // the DCT preconditioner: D H^T with H^T the orthonormal DCT-III (dct.cu)
+    if (c.flags & SK_FLAG_DCT) return launch_dct_inverse(c, in, r, out, f64, s);
     const int threads = c.pt >= 512 ? 512 : (c.pt >= 32 ? (int)c.pt : 32);
     int blocks = (int)(r < 1024 ? r : 1024);
     const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);

@@ -159,6 +159,21 @@ def covariance(ctx: sk.Ctx, idx, val, mode: int, G=None, C=None, work=None):
     return sk.sk_cov_finalize(ctx, G, idx.shape[0], C=C)
 
 
+def covariance_centred(ctx: sk.Ctx, idx, val, mode: int, G=None, C=None, work=None):
+    """Centred covariance estimate of one batch of ELL rows: C_n (Sec. V) and
+    the sample mean (Sec. IV) of the same rows, combined with the correction
+    that makes C_n - xbar xbar^T unbiased.  Returns (C, mean)."""
+    n = idx.shape[0]
+    if G is None:
+        G = torch.empty((ctx.pt, ctx.pt), dtype=torch.float64, device=idx.device)
+    sk.sk_cov_reset(ctx, G)
+    sk.sk_cov_accumulate(ctx, mode, idx, val, G, work=work)
+    sums = torch.zeros(ctx.pt, dtype=torch.float64, device=idx.device)
+    sk.sk_mean_accumulate(ctx, idx, val, sums)
+    mean = sk.sk_mean_finalize(ctx, sums, n)
+    return sk.sk_cov_finalize_centred(ctx, G, mean, n, C=C), mean
+
+
 class HostStreamer:
     """Compress host rows and add them to the Gram while they stream to the
     device (Algorithm 1's one pass over X, Sec. V's G = sum of w w^T).

@@ -44,7 +44,7 @@ def test_host_validation_without_gpu():
     lib.sk_destroy(h)
     lib.sk_destroy(nul)
     # flags: the ablation bit is accepted, unknown bits are not
-    assert lib.sk_init_ex(ctypes.byref(h), 100, 5, 1, 2) == _lib.SK_EINVAL
+    assert lib.sk_init_ex(ctypes.byref(h), 100, 5, 1, 4) == _lib.SK_EINVAL
     assert lib.sk_init_ex(ctypes.byref(h), 100, 5, 1, _lib.SK_FLAG_NO_PRECONDITION) == _lib.SK_OK
     assert lib.sk_flags(h) == _lib.SK_FLAG_NO_PRECONDITION
     assert lib.sk_kmeans2_assign(h, nul, 4, 100, nul, 3, nul, nul, nul) == _lib.SK_EINVAL
@@ -53,6 +53,18 @@ def test_host_validation_without_gpu():
     assert lib.sk_mean_finalize(h, nul, 0, nul, nul) == _lib.SK_EINVAL
     lib.sk_destroy(h)
     assert lib.sk_flags(nul) == 0
+    # the DCT preconditioner: even p with p / 2 13-smooth, pt = p, not with the ablation
+    assert lib.sk_init_ex(ctypes.byref(h), 784, 39, 1, _lib.SK_FLAG_DCT) == _lib.SK_OK
+    assert lib.sk_ptilde(h) == 784
+    lib.sk_destroy(h)
+    assert lib.sk_init_ex(ctypes.byref(h), 785, 39, 1, _lib.SK_FLAG_DCT) == _lib.SK_EUNSUPPORTED
+    assert lib.sk_init_ex(ctypes.byref(h), 2 * 17, 4, 1, _lib.SK_FLAG_DCT) == _lib.SK_EUNSUPPORTED
+    assert lib.sk_init_ex(ctypes.byref(h), 784, 4, 1,
+                          _lib.SK_FLAG_DCT | _lib.SK_FLAG_NO_PRECONDITION) == _lib.SK_EINVAL
+    it = _lib.SkBatchItem(p=1000, m=50, seed=1, flags=_lib.SK_FLAG_DCT, n=10, ldx=1000, K=3)
+    bb = ctypes.c_void_p(0)
+    assert lib.sk_batch_create(ctypes.byref(bb), ctypes.cast(ctypes.pointer(it), ctypes.c_void_p),
+                               1, _lib.SK_GRAM_BF16) == _lib.SK_EUNSUPPORTED
     # batch plans validate their items on the host before any CUDA call
     it = _lib.SkBatchItem(p=100, m=5, seed=1, n=10, ldx=100, K=3)
     b = ctypes.c_void_p(0)

@@ -87,7 +87,7 @@ def test_no_preconditioning_precondition_and_unmix_are_pad_and_truncate(sk):
 
 def test_init_ex_rejects_unknown_flags(sk):
     with pytest.raises(sk.SkError) as e:
-        sk.sk_init_ex(100, 5, 1, 2)
+        sk.sk_init_ex(100, 5, 1, 4)
     assert e.value.status == sk.SK_EINVAL
 
 
@@ -253,3 +253,38 @@ def test_hk_deviation_matches_oracle(sk):
     assert np.array_equal(cnt.cpu().numpy(), counts_o)
     assert np.abs(dev.cpu().numpy() - ref).max() <= 1e-14
     assert dev[K - 1].item() == -1.0
+
+
+@pytest.mark.parametrize("p,m,n,mode", [(64, 8, 2000, 0), (256, 13, 3000, 2), (1000, 50, 1500, 2),
+                                        (1024, 51, 4000, 0), (4096, 205, 300, 2)])
+def test_cov_centred_matches_oracle(p, m, n, mode):
+    """Centred covariance estimate (C_n - xbar xbar^T + B(C_n)/n) against the
+    FP64 oracle on the same seeded rows, accumulated over two chunks:
+    relative Frobenius <= 1e-6 (FP32 Gram) or 1e-5 (split-BF16 Gram)."""
+    import oracle
+    from paper_1511_00152_gb300 import _lib as sk
+    X = synth.lowrank_spiky(n, p, seed=p + n) + 0.5
+    seed = 19
+    ctx = sk.sk_init(p, m, seed)
+    idx, val = sk.sk_compress(ctx, torch.as_tensor(X, device="cuda"))
+    G = torch.zeros((ctx.pt, ctx.pt), dtype=torch.float64, device="cuda")
+    sums = torch.zeros(ctx.pt, dtype=torch.float64, device="cuda")
+    h = n // 3
+    for a, b in ((0, h), (h, n)):
+        sk.sk_cov_accumulate(ctx, mode, idx[a:b].contiguous(), val[a:b].contiguous(), G)
+        sk.sk_mean_accumulate(ctx, idx[a:b].contiguous(), val[a:b].contiguous(), sums)
+    mean = sk.sk_mean_finalize(ctx, sums, n)
+    C = sk.sk_cov_finalize_centred(ctx, G, mean, n)
+    torch.cuda.synchronize()
+    oi, ov = oracle.compress(X, m, seed)
+    Co = oracle.cov_centred(oracle.gram(oi, ov, ctx.pt), oracle.sample_mean(oi, ov, ctx.pt), n, m)
+    tol = 1e-6 if mode == 0 else 1e-5
+    Cg = C.cpu().numpy()
+    assert np.allclose(Cg, Cg.T)
+    assert np.linalg.norm(Cg - Co) <= tol * np.linalg.norm(Co)
+    # the pipeline helper gives the same estimate
+    from paper_1511_00152_gb300 import pipeline
+    C2, mean2 = pipeline.covariance_centred(ctx, idx, val, mode)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(C2.cpu().numpy() - Co) <= tol * np.linalg.norm(Co)
+    assert sk.sk_device_status() == sk.SK_OK
