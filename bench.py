@@ -615,7 +615,8 @@ def run_gpu(args, cfg):
         del X, Xsel, idx, val, G, C, gwork, st, work
         torch.cuda.empty_cache()
         extra = {}
-        for name, fn in (("pca", run_pca), ("serving", run_serving), ("batching", run_batching)):
+        for name, fn in (("pca", run_pca), ("serving", run_serving), ("batching", run_batching),
+                         ("dct", run_dct)):
             try:
                 extra[name] = fn(args, standalone=False)
             except Exception as exc:  # report, do not hide
@@ -864,6 +865,78 @@ def run_pca(args, standalone=True):
     return 0
 
 
+# ------------------------------------------------------------------ DCT
+
+DCT = dict(workload="dct_mixture_n1e6_p784_m39_K10", n=1_000_000, p=784, m=39, K=10, iters=10,
+           seed=784)
+
+
+def run_dct(args, standalone=True):
+    """The DCT preconditioner (no padding) on the paper's MNIST-sized samples
+    (p = 784, gamma = 5%): compress against its HBM roofline (4p + 8m bytes
+    per row), beside the Hadamard form of the same rows (zero-padded to 1024),
+    and K-means iterations at pt = 784."""
+    import torch
+    from paper_1511_00152_gb300 import build as skbuild
+    skbuild.build()
+    from paper_1511_00152_gb300 import _lib as sk
+    from paper_1511_00152_gb300 import pipeline, synth
+    cfg = dict(DCT)
+    n, p, m, K = cfg["n"], cfg["p"], cfg["m"], cfg["K"]
+    X, _, _ = synth.mixture_device(n, p, K, cfg["seed"])
+    hbm, bf16, bf16s, src = load_peaks()
+    sampler = ClockSampler(torch.cuda.current_device())
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ctx = sk.sk_init_ex(p, m, cfg["seed"], sk.SK_FLAG_DCT)
+    ctx_h = sk.sk_init(p, m, cfg["seed"])
+    idx = torch.empty((n, m), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    sampler.start()
+    t_dct = timed(lambda: sk.sk_compress(ctx, X, idx=idx, val=val))
+    t_had = timed(lambda: sk.sk_compress(ctx_h, X, idx=torch.empty_like(idx),
+                                         val=torch.empty_like(val)))
+    sk.sk_compress(ctx, X, idx=idx, val=val)
+    rows = synth.init_rows(n, K, cfg["seed"])
+    mu0 = sk.sk_precondition(ctx, X[torch.as_tensor(rows, device="cuda")].contiguous())
+    st = pipeline.KMeansState(ctx, n, K)
+    st.run(idx, val, mu0, cfg["iters"], use_graph=True)
+    t_km = timed(lambda: st.run(idx, val, mu0, cfg["iters"], use_graph=True), reps=3)
+    clocks = sampler.stop()
+    assert sk.sk_device_status() == sk.SK_OK
+    bytes_row = 4 * p + 8 * m
+    line = {
+        "metric": "DCT preconditioner (no padding): compress samples/s and %HBM, K-means iteration",
+        "value": n / (t_dct * 1e-3), "unit": "samples/s (compress)", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "n": n, "p": p, "pt": ctx.pt, "m": m, "K": K,
+                   "kmeans_iters": cfg["iters"]},
+        "compress_dct": {"ms": t_dct, "achieved_gbs": n * bytes_row / (t_dct * 1e-3) / 1e9,
+                         "frac_hbm": n * bytes_row / (t_dct * 1e-3) / 1e9 / hbm},
+        "compress_hadamard_padded_1024": {"ms": t_had,
+                                          "achieved_gbs": n * bytes_row / (t_had * 1e-3) / 1e9},
+        "kmeans_iter_ms": t_km / cfg["iters"],
+        "kmeans_frac_hbm": n * (8 * m + 8) / (t_km / cfg["iters"] * 1e-3) / 1e9 / hbm,
+        "peak_source": src, "clocks": clocks,
+    }
+    del X, idx, val, st
+    if not standalone:
+        return line
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ batching
 
 BATCHING = dict(workload="batch64_mixtures_p256-8192_n1e4-5e5", datasets=64, iters=15,
@@ -999,9 +1072,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the K-means loop kernel by kernel (for profilers)")
     ap.add_argument("--workload", default="kmeans",
-                    choices=["kmeans", "serving", "batching", "pca"],
+                    choices=["kmeans", "serving", "batching", "pca", "dct"],
                     help="kmeans: the main step (default); serving: the streaming request loop; "
-                         "batching: 64 data sets, one launch per stage; pca: the PCA workload")
+                         "batching: 64 data sets, one launch per stage; pca: the PCA workload; "
+                         "dct: the DCT preconditioner at p = 784")
     args = ap.parse_args()
     if args.workload == "serving" and args.impl != "reference":
         return run_serving(args)
@@ -1009,6 +1083,8 @@ def main():
         return run_batching(args)
     if args.workload == "pca" and args.impl != "reference":
         return run_pca(args)
+    if args.workload == "dct" and args.impl != "reference":
+        return run_dct(args)
     cfg = dict(WORKLOAD)
     if args.n:
         cfg["n"] = args.n
