@@ -91,6 +91,7 @@ struct DctParams {
     float *val;          // forward gather: output (n x m)
     void *out;           // forward dense: Y (float, n x N); inverse: rows (T, n x N)
     int m;
+    int vec;             // forward: rows 16-byte aligned with N % 4 == 0 (float4 loads)
 };
 
 // Twiddle exp(-2 pi i dir t / L): dir = 1 forward, -1 inverse; from the
@@ -211,15 +212,60 @@ __global__ void __launch_bounds__(512) dct_forward_kernel(DctParams P) {
     const Twiddle<float, true> twf{tw, L, 1.f};
     const float s0 = sqrtf(1.f / (float)N), s1 = sqrtf(2.f / (float)N);
     const float *X = static_cast<const float *>(P.in);
-    for (int64_t i = blockIdx.x; i < P.n; i += gridDim.x) {
-        // u = D x in the reordered sequence v, read as the floats of z
-        float *zf = reinterpret_cast<float *>(b0);
+    // Each thread holds up to kPF float4 (or 4 kPF floats) of a row: every
+    // thread's part of a row is loaded at once, and the next row's part is
+    // loaded while this row is transformed (N / 4 <= kPF blockDim.x by the
+    // launch's choice of blockDim.x).
+    constexpr int kPF = 4;
+    float4 pre[kPF];
+    auto load_row = [&](int64_t i) {
+        if (i >= P.n) return;
         const float *xr = X + i * P.ldx;
-        for (int l = tid; l < N; l += nthr) {
-            float u = __ldcs(xr + l);
-            if (sign_neg(sgn, l)) u = -u;
-            const int q = (l & 1) ? N - 1 - (l >> 1) : (l >> 1);
-            zf[q] = u;
+        if (P.vec) {
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) {
+                const int e = tid + u * nthr;
+                if (4 * e < N) pre[u] = __ldcs(reinterpret_cast<const float4 *>(xr) + e);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) {
+                const int l = 4 * (tid + u * nthr);
+                pre[u].x = l + 0 < N ? __ldcs(xr + l + 0) : 0.f;
+                pre[u].y = l + 1 < N ? __ldcs(xr + l + 1) : 0.f;
+                pre[u].z = l + 2 < N ? __ldcs(xr + l + 2) : 0.f;
+                pre[u].w = l + 3 < N ? __ldcs(xr + l + 3) : 0.f;
+            }
+        }
+    };
+    load_row(blockIdx.x);
+    for (int64_t i = blockIdx.x; i < P.n; i += gridDim.x) {
+        // u = D x in the reordered sequence v, written as the floats of z
+        float *zf = reinterpret_cast<float *>(b0);
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const int l0 = 4 * (tid + u * nthr);
+            const float xs[4] = {pre[u].x, pre[u].y, pre[u].z, pre[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int l = l0 + c;
+                if (l < N) {
+                    const float x = sign_neg(sgn, l) ? -xs[c] : xs[c];
+                    zf[(l & 1) ? N - 1 - (l >> 1) : (l >> 1)] = x;
+                }
+            }
+        }
+        // the next row's loads fly during this row's transform; this row's
+        // masks are fetched early too
+        load_row(i + gridDim.x);
+        int jm[4];
+        if constexpr (!DENSE) {
+            const int32_t *gi = P.idx + i * P.m;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = tid + u * nthr;
+                jm[u] = t < P.m ? __ldcg(gi + t) : 0;
+            }
         }
         __syncthreads();
         float2 *Z = fft(b0, b1, P, twf, tid, nthr);
@@ -242,7 +288,12 @@ __global__ void __launch_bounds__(512) dct_forward_kernel(DctParams P) {
         } else {
             const int32_t *gi = P.idx + i * P.m;
             float *ov = P.val + i * P.m;
-            for (int t = tid; t < P.m; t += nthr) ov[t] = y[clamp_index(__ldcg(gi + t), N)];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = tid + u * nthr;
+                if (t < P.m) ov[t] = y[clamp_index(jm[u], N)];
+            }
+            for (int t = tid + 4 * nthr; t < P.m; t += nthr) ov[t] = y[clamp_index(__ldcg(gi + t), N)];
         }
         __syncthreads();
     }
@@ -305,8 +356,10 @@ __global__ void __launch_bounds__(512) dct_inverse_kernel(DctParams P) {
     }
 }
 
+// Threads per row: about one per 8 of the FFT's L points (whole warps, 64 to
+// 512), so that a row's N = 2L floats are at most 4 float4 per thread.
 int dct_threads(int L) {
-    int t = (L / 8 + 31) / 32 * 32;
+    int t = ((L + 7) / 8 + 31) / 32 * 32;
     if (t < 64) t = 64;
     if (t > 512) t = 512;
     return t;
@@ -382,6 +435,7 @@ cudaError_t launch_dct_forward(const sk_ctx &c, const float *X, int64_t n, int64
     P.in = X;
     P.n = n;
     P.ldx = ldx;
+    P.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (c.p % 4 == 0) && (ldx % 4 == 0);
     P.idx = idx;
     P.val = val;
     P.out = Y;
