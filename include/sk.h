@@ -252,7 +252,7 @@ sk_status sk_kmeans_step_delta(const sk_ctx *ctx, const int32_t *idx, const floa
  * call can sit in a captured CUDA graph.  state: device int64[2], caller-
  * owned; state[0] carries from one pass to the next the number of rows
  * whose label changed, state[1] is scratch.  The pass is a full rebuild if
- * first != 0 or state[0] > n / 16 (many moved rows: moving each one's
+ * first != 0 or state[0] > n / 12 (many moved rows: moving each one's
  * entries with global atomics would cost more than rebuilding the sums in
  * shared memory), else incremental.  On return labels, S, cnt, nk describe
  * the new assignment and state[0] holds this pass's count of changed rows

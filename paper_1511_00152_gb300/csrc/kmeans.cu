@@ -1050,7 +1050,7 @@ cudaError_t launch_kmeans_auto(const sk_ctx &c, const int32_t *idx, const float 
                                double *S, int32_t *cnt, int64_t *nk, int64_t *state, int first,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    kmeans_auto_decide_kernel<<<1, 1024, 0, s>>>(state, n / 16, first, (int64_t)K * c.pt, K, S,
+    kmeans_auto_decide_kernel<<<1, 1024, 0, s>>>(state, n / 12, first, (int64_t)K * c.pt, K, S,
                                                  cnt, nk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
