@@ -19,11 +19,12 @@
 // DFT and writes output q to (j / Ns) Ns R + k + q Ns.  Supported radices are
 // 2, 3, 4, 5, 7, 8, 11, 13 (the factorisation of L is made at sk_init_ex).
 //
-// Forward rows (compress and precondition) are the hot path: one CTA per row
-// at a time, persistent over rows, with the FFT twiddles and the two
-// post-processing phase tables computed once per CTA in float32; the mask of
-// each row has already been drawn (mask_kernel, range p) and the CTA gathers
-// val = y[idx].  Un-mixing (few rows) computes its twiddles as it goes, in
+// Forward rows (compress and precondition) are the hot path: one warp per
+// row for p <= 1024 (no block-wide barriers; the CTA's warps share the
+// tables), else one CTA per row at a time, persistent over rows, with the
+// FFT twiddles and the two post-processing phase tables computed once per CTA
+// in float32; the mask of each row has already been drawn (mask_kernel,
+// range p) and the row's warp or CTA gathers val = y[idx].  Un-mixing (few rows) computes its twiddles as it goes, in
 // float32 or float64.
 #include <cstring>
 
@@ -158,7 +159,7 @@ __device__ __forceinline__ void fft_stage(const C2 *in, C2 *out, int L, int Ns, 
 
 // FFT of a (L complex) using b as the other buffer; returns the buffer that
 // holds the result.  The CTA's threads take part; syncs between stages.
-template <typename C2, typename TW>
+template <typename C2, typename TW, bool WARP = false>
 __device__ C2 *fft(C2 *a, C2 *b, const DctParams &P, const TW &tw, int tid, int nthr) {
     int Ns = 1;
     for (int s = 0; s < P.nf; ++s) {
@@ -173,7 +174,11 @@ __device__ C2 *fft(C2 *a, C2 *b, const DctParams &P, const TW &tw, int tid, int 
             case 11: fft_stage<11>(a, b, P.L, Ns, tw, tid, nthr); break;
             default: fft_stage<13>(a, b, P.L, Ns, tw, tid, nthr); break;
         }
-        __syncthreads();
+        if constexpr (WARP) {
+            __syncwarp();
+        } else {
+            __syncthreads();
+        }
         C2 *t = a;
         a = b;
         b = t;
@@ -296,6 +301,102 @@ __global__ void __launch_bounds__(512) dct_forward_kernel(DctParams P) {
             for (int t = tid + 4 * nthr; t < P.m; t += nthr) ov[t] = y[clamp_index(__ldcg(gi + t), N)];
         }
         __syncthreads();
+    }
+}
+
+// Forward rows, one warp per row (N <= 1024): the CTA's warps share the
+// twiddle and phase tables and each keeps its own two FFT buffers, so a row
+// needs no block-wide barrier; a lane holds up to 8 float4 of a row and loads
+// the next row's while this one is transformed.
+constexpr int kWarpRowsMaxN = 1024;
+constexpr int kWarpRowsWarps = 8;
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kWarpRowsWarps * 32, 2) dct_forward_warp_kernel(DctParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = P.N, L = P.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *tw = reinterpret_cast<float2 *>(smem_raw);  // L
+    float2 *ph = tw + L;                                 // L + 1
+    float2 *om = ph + (L + 1);                           // L + 1
+    uint32_t *sgn = reinterpret_cast<uint32_t *>(om + (L + 1));  // 2 ceil(N / 64) words
+    const int sgn_words = 2 * ((N + 63) / 64);
+    float2 *b0 = reinterpret_cast<float2 *>(sgn + sgn_words) + (size_t)warp * 2 * L;
+    float2 *b1 = b0 + L;
+    for (int t = tid; t < L; t += blockDim.x) tw[t] = expipi((float)(2 * t) / (float)L, -1.f);
+    for (int k = tid; k <= L; k += blockDim.x) {
+        ph[k] = expipi((float)k / (float)(2 * N), -1.f);
+        om[k] = expipi((float)(2 * k) / (float)N, -1.f);
+    }
+    for (int w = tid; w < (N + 31) / 32; w += blockDim.x) {
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)(w >> 2), 0u, 0u, kTagSign), P.k0, P.k1);
+        sgn[w] = pick_word(o, (uint32_t)w & 3u);
+    }
+    __syncthreads();
+    const Twiddle<float, true> twf{tw, L, 1.f};
+    const float s0 = sqrtf(1.f / (float)N), s1 = sqrtf(2.f / (float)N);
+    const float *X = static_cast<const float *>(P.in);
+    constexpr int kPF = kWarpRowsMaxN / 4 / 32;  // float4 per lane
+    float4 pre[kPF];
+    auto load_row = [&](int64_t i) {
+        if (i >= P.n) return;
+        const float *xr = X + i * P.ldx;
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const int e = lane + 32 * u;
+            if (P.vec) {
+                if (4 * e < N) pre[u] = __ldcs(reinterpret_cast<const float4 *>(xr) + e);
+            } else {
+                const int l = 4 * e;
+                pre[u].x = l + 0 < N ? __ldcs(xr + l + 0) : 0.f;
+                pre[u].y = l + 1 < N ? __ldcs(xr + l + 1) : 0.f;
+                pre[u].z = l + 2 < N ? __ldcs(xr + l + 2) : 0.f;
+                pre[u].w = l + 3 < N ? __ldcs(xr + l + 3) : 0.f;
+            }
+        }
+    };
+    const int64_t gw = (int64_t)blockIdx.x * kWarpRowsWarps + warp;
+    const int64_t nw = (int64_t)gridDim.x * kWarpRowsWarps;
+    load_row(gw);
+    for (int64_t i = gw; i < P.n; i += nw) {
+        float *zf = reinterpret_cast<float *>(b0);
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const int l0 = 4 * (lane + 32 * u);
+            const float xs[4] = {pre[u].x, pre[u].y, pre[u].z, pre[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int l = l0 + c;
+                if (l < N) {
+                    const float x = sign_neg(sgn, l) ? -xs[c] : xs[c];
+                    zf[(l & 1) ? N - 1 - (l >> 1) : (l >> 1)] = x;
+                }
+            }
+        }
+        load_row(i + nw);
+        __syncwarp();
+        float2 *Z = fft<float2, Twiddle<float, true>, true>(b0, b1, P, twf, lane, 32);
+        float *y = reinterpret_cast<float *>(Z == b0 ? b1 : b0);
+        for (int k = lane; k <= L; k += 32) {
+            const float2 Zk = Z[k == L ? 0 : k];
+            const float2 Zc = cconj(Z[k == 0 ? 0 : L - k]);
+            const float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
+            const float2 O = make_float2(0.5f * (Zk.y - Zc.y), -0.5f * (Zk.x - Zc.x));
+            const float2 V = cadd(E, cmul(om[k], O));
+            const float2 W = cmul(ph[k], V);
+            if (k < N) y[k] = (k == 0 ? s0 : s1) * W.x;
+            if (k > 0 && k < L) y[N - k] = s1 * (-W.y);
+        }
+        __syncwarp();
+        if constexpr (DENSE) {
+            float *Y = static_cast<float *>(P.out) + i * N;
+            for (int k = lane; k < N; k += 32) Y[k] = y[k];
+        } else {
+            const int32_t *gi = P.idx + i * P.m;
+            float *ov = P.val + i * P.m;
+            for (int t = lane; t < P.m; t += 32) ov[t] = y[clamp_index(__ldcg(gi + t), N)];
+        }
+        __syncwarp();
     }
 }
 
@@ -439,6 +540,26 @@ cudaError_t launch_dct_forward(const sk_ctx &c, const float *X, int64_t n, int64
     P.idx = idx;
     P.val = val;
     P.out = Y;
+    if (c.p <= kWarpRowsMaxN) {
+        // a warp per row: per CTA the shared tables, per warp two buffers
+        const size_t L = (size_t)P.L;
+        const size_t smem = (3 * L + 2) * sizeof(float2) + 2 * (((size_t)c.p + 63) / 64) * 4 +
+                            (size_t)kWarpRowsWarps * 2 * L * sizeof(float2);
+        auto kern = Y ? dct_forward_warp_kernel<true> : dct_forward_warp_kernel<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpRowsWarps * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t blocks = (int64_t)sms * per_sm;
+        const int64_t need = (n + kWarpRowsWarps - 1) / kWarpRowsWarps;
+        if (blocks > need) blocks = need;
+        kern<<<(unsigned)blocks, kWarpRowsWarps * 32, smem, s>>>(P);
+        return cudaGetLastError();
+    }
     const size_t smem = dct_forward_smem(c);
     return Y ? launch_rows(dct_forward_kernel<true>, P, smem, s)
              : launch_rows(dct_forward_kernel<false>, P, smem, s);
