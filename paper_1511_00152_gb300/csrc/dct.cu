@@ -112,10 +112,31 @@ struct Twiddle {
     }
 };
 
+// Radix-4 butterfly on x0..x3 (w_4 = -i dir), outputs in natural order.
+template <typename C2, typename R>
+__device__ __forceinline__ void dft4(C2 x0, C2 x1, C2 x2, C2 x3, R dir, C2 &y0, C2 &y1, C2 &y2,
+                                     C2 &y3) {
+    const C2 a = cadd(x0, x2), b = csub(x0, x2);
+    const C2 c = cadd(x1, x3), d = csub(x1, x3);
+    C2 dm;  // d times -i dir
+    dm.x = d.y * dir;
+    dm.y = -d.x * dir;
+    y0 = cadd(a, c);
+    y2 = csub(a, c);
+    y1 = cadd(b, dm);
+    y3 = csub(b, dm);
+}
+
 // One Stockham stage of radix R: in -> out (both L complex in shared memory).
+// Radix 2, 4 and 8 are written out; an odd radix uses the symmetric form of
+// the R-point DFT: with a_r = x_r + x_{R-r}, b_r = x_r - x_{R-r} (r <= H =
+// (R-1)/2), y_q = x_0 + sum_r a_r cos(2 pi r q / R) - i dir sum_r b_r
+// sin(2 pi r q / R) and y_{R-q} the same with + i dir, a quarter of the
+// multiplications of the direct sum.
 template <int R, typename C2, typename TW>
 __device__ __forceinline__ void fft_stage(const C2 *in, C2 *out, int L, int Ns, const TW &tw,
                                           int tid, int nthr) {
+    using T = decltype(C2().x);
     const int S = L / R;
     const int st = L / (Ns * R);  // twiddle stride: k r st < L
     C2 rt[R];                     // the R-th roots of unity, rt[s] = w_R^s
@@ -127,31 +148,74 @@ __device__ __forceinline__ void fft_stage(const C2 *in, C2 *out, int L, int Ns, 
         C2 x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = in[j + r * S];
+        if (Ns > 1) {  // the first stage's twiddles are all 1
 #pragma unroll
-        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw(k * r * st));
+            for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw(k * r * st));
+        }
         const int base = jq * Ns * R + k;
         if constexpr (R == 2) {
             out[base] = cadd(x[0], x[1]);
             out[base + Ns] = csub(x[0], x[1]);
         } else if constexpr (R == 4) {
-            const C2 a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
-            const C2 c = cadd(x[1], x[3]), d = csub(x[1], x[3]);
-            // d times w_4 = exp(-2 pi i dir / 4) = -i dir
-            C2 dm;
-            dm.x = d.y * tw.dir;
-            dm.y = -d.x * tw.dir;
-            out[base] = cadd(a, c);
-            out[base + 2 * Ns] = csub(a, c);
-            out[base + Ns] = cadd(b, dm);
-            out[base + 3 * Ns] = csub(b, dm);
+            C2 y0, y1, y2, y3;
+            dft4(x[0], x[1], x[2], x[3], tw.dir, y0, y1, y2, y3);
+            out[base] = y0;
+            out[base + Ns] = y1;
+            out[base + 2 * Ns] = y2;
+            out[base + 3 * Ns] = y3;
+        } else if constexpr (R == 8) {
+            // two radix-4 DFTs of the even and odd inputs, then w_8^q
+            C2 e0, e1, e2, e3, o0, o1, o2, o3;
+            dft4(x[0], x[2], x[4], x[6], tw.dir, e0, e1, e2, e3);
+            dft4(x[1], x[3], x[5], x[7], tw.dir, o0, o1, o2, o3);
+            const T h = (T)0.70710678118654752440;
+            C2 t1, t2, t3;  // o1 w_8, o2 w_8^2, o3 w_8^3 with w_8 = h (1 - i dir)
+            t1.x = h * (o1.x + tw.dir * o1.y);
+            t1.y = h * (o1.y - tw.dir * o1.x);
+            t2.x = tw.dir * o2.y;
+            t2.y = -tw.dir * o2.x;
+            t3.x = h * (-o3.x + tw.dir * o3.y);
+            t3.y = h * (-o3.y - tw.dir * o3.x);
+            out[base] = cadd(e0, o0);
+            out[base + 4 * Ns] = csub(e0, o0);
+            out[base + Ns] = cadd(e1, t1);
+            out[base + 5 * Ns] = csub(e1, t1);
+            out[base + 2 * Ns] = cadd(e2, t2);
+            out[base + 6 * Ns] = csub(e2, t2);
+            out[base + 3 * Ns] = cadd(e3, t3);
+            out[base + 7 * Ns] = csub(e3, t3);
         } else {
-            // the R-point DFT, one output at a time: y_q = sum_r x_r w_R^(r q)
+            constexpr int H = (R - 1) / 2;
+            C2 a[H + 1], b[H + 1];
+            C2 y0 = x[0];
 #pragma unroll
-            for (int q = 0; q < R; ++q) {
-                C2 acc = x[0];
+            for (int r = 1; r <= H; ++r) {
+                a[r] = cadd(x[r], x[R - r]);
+                b[r] = csub(x[r], x[R - r]);
+                y0 = cadd(y0, a[r]);
+            }
+            out[base] = y0;
 #pragma unroll
-                for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(x[r], rt[(r * q) % R]));
-                out[base + q * Ns] = acc;
+            for (int q = 1; q <= H; ++q) {
+                C2 re = x[0], im;
+                im.x = (T)0;
+                im.y = (T)0;
+#pragma unroll
+                for (int r = 1; r <= H; ++r) {
+                    const C2 w = rt[(r * q) % R];  // (cos, -dir sin) of 2 pi r q / R
+                    re.x += a[r].x * w.x;
+                    re.y += a[r].y * w.x;
+                    im.x -= b[r].x * w.y;  // b_r dir sin
+                    im.y -= b[r].y * w.y;
+                }
+                // y_q = re - i im, y_{R-q} = re + i im
+                C2 yq, yr;
+                yq.x = re.x + im.y;
+                yq.y = re.y - im.x;
+                yr.x = re.x - im.y;
+                yr.y = re.y + im.x;
+                out[base + q * Ns] = yq;
+                out[base + (R - q) * Ns] = yr;
             }
         }
     }

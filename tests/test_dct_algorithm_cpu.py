@@ -5,7 +5,8 @@ take (2, 3, 4, 5, 7, 8, 11, 13) -- the GPU tests cover a few lengths only.
 
 Forward: the even/odd reordering into z of length L = N/2, the self-sorting
 mixed-radix FFT with the kernel's stage addressing (input j + r S, twiddle
-index k r st, output (j / Ns) Ns R + k + q Ns), then E, O, V, W and
+index k r st, output (j / Ns) Ns R + k + q Ns) and its butterflies (radix
+2, 4 and 8 written out, odd radices in the symmetric form), then E, O, V, W and
 X_k = Re W_k, X_{N-k} = -Im W_k.  Inverse: the same steps backwards with the
 inverse FFT, as the un-mixing kernel runs them."""
 import numpy as np
@@ -29,6 +30,37 @@ def factor(L):
     return out
 
 
+def dft4(x0, x1, x2, x3, d):
+    a, b, c, e = x0 + x2, x0 - x2, x1 + x3, x1 - x3
+    em = -1j * d * e
+    return a + c, b + em, a - c, b - em
+
+
+def butterfly(x, R, d, rt):
+    """The kernels' R-point DFT: radix 2, 4, 8 written out, odd R in the
+    symmetric form (a_r = x_r + x_{R-r}, b_r = x_r - x_{R-r})."""
+    if R == 2:
+        return [x[0] + x[1], x[0] - x[1]]
+    if R == 4:
+        return list(dft4(*x, d))
+    if R == 8:
+        e = dft4(x[0], x[2], x[4], x[6], d)
+        o = dft4(x[1], x[3], x[5], x[7], d)
+        h = np.sqrt(0.5)
+        t = [o[0], h * (1 - 1j * d) * o[1], -1j * d * o[2], h * (-1 - 1j * d) * o[3]]
+        return [e[q] + t[q] for q in range(4)] + [e[q] - t[q] for q in range(4)]
+    H = (R - 1) // 2
+    a = [None] + [x[r] + x[R - r] for r in range(1, H + 1)]
+    b = [None] + [x[r] - x[R - r] for r in range(1, H + 1)]
+    y = [None] * R
+    y[0] = x[0] + sum(a[1:])
+    for q in range(1, H + 1):
+        re = x[0] + sum(a[r] * rt[(r * q) % R].real for r in range(1, H + 1))
+        im = sum(b[r] * -rt[(r * q) % R].imag for r in range(1, H + 1))
+        y[q], y[R - q] = re - 1j * im, re + 1j * im
+    return y
+
+
 def fft_stockham(z, direction):
     L = len(z)
     tw = np.exp(-direction * 2j * np.pi * np.arange(L) / L)
@@ -39,10 +71,13 @@ def fft_stockham(z, direction):
         rt = tw[np.arange(R) * S]
         for j in range(S):
             jq, k = divmod(j, Ns)
-            x = a[j + np.arange(R) * S] * tw[k * np.arange(R) * st]
+            x = a[j + np.arange(R) * S]
+            if Ns > 1:
+                x = x * tw[k * np.arange(R) * st]
+            y = butterfly(list(x), R, direction, rt)
             base = jq * Ns * R + k
             for q in range(R):
-                b[base + q * Ns] = np.sum(x * rt[(np.arange(R) * q) % R])
+                b[base + q * Ns] = y[q]
         a, Ns = b, Ns * R
     return a
 
