@@ -61,10 +61,10 @@ UNIT = "samples/s"
 # dominant kernel from one ncu capture of this workload, valid only while the
 # kernel source still has the digest it had when captured.
 KERNEL_TRAFFIC = {
-    # 164.88 MB read + 3.92 MB written per incremental pass at n = 400,000
-    # (422.0 B per row), scaled to n = 10^6
-    "kmeans": {"bytes": 422_000_000, "n": 1_000_000, "p": 1024,
-               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "7710672b8470aee7"},
+    # kmeans_rc_kernel: 164.87 MB read + 3.82 MB written per incremental pass
+    # at n = 400,000 (421.7 B per row), scaled to n = 10^6
+    "kmeans": {"bytes": 421_700_000, "n": 1_000_000, "p": 1024,
+               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "36541619474fa12e"},
 }
 
 
@@ -455,7 +455,8 @@ def run_gpu(args, cfg):
         # read the ELL row (8m B) and the previous label (4 B), write the label (4 B);
         # the per-iteration time is the graph's / iters, so it includes one
         # finalize launch (and the first, full-sums pass is averaged in)
-        "kmeans": {"kernel": "kmeans_kernel (assign + incremental update)", "bound": "hbm",
+        "kmeans": {"kernel": "kmeans_rc_kernel (assignment + incremental sums; rebuilds add "
+                             "kmeans_sums_kernel)", "bound": "hbm",
                    "bytes": n * (8 * m + 8), "ms": kmeans_iter_ms, "peak": hbm, "unit": "GB/s"},
     }
     if prods:
