@@ -61,10 +61,16 @@ UNIT = "samples/s"
 # dominant kernel from one ncu capture of this workload, valid only while the
 # kernel source still has the digest it had when captured.
 KERNEL_TRAFFIC = {
-    # kmeans_rc_kernel: 164.87 MB read + 3.82 MB written per incremental pass
-    # at n = 400,000 (421.7 B per row), scaled to n = 10^6
-    "kmeans": {"bytes": 421_700_000, "n": 1_000_000, "p": 1024,
-               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "36541619474fa12e"},
+    # kmeans_rc_kernel: 164.87 MB read + 3.88 MB written per incremental pass
+    # at n = 400,000 (421.9 B per row), scaled to n = 10^6
+    "kmeans": {"bytes": 421_900_000, "n": 1_000_000, "p": 1024,
+               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "d2f00a6be855b224"},
+    # gram_tc_kernel (split-BF16): 178.28 MB read + 9.86 MB written per launch
+    # at n = 400,000; the reads (the ELL rows, read once from DRAM by all of a
+    # row range's tiles) scaled to n = 10^6, the writes (the float64 Gram's
+    # atomics) kept
+    "gram": {"bytes": 455_600_000, "n": 1_000_000, "p": 1024,
+             "source": "paper_1511_00152_gb300/csrc/gram_tc.cu", "src_sha": "7208d7883a2122bd"},
 }
 
 
