@@ -382,7 +382,7 @@ def run_gpu(args, cfg):
     # finalize)
     launches = {"compress": 1, "gram": 1 if args.gram == "fp32" else 2, "cov_finalize": 1,
                 "topk": 4 * max(args.topk_iters, 1) + 6 + (1 if args.topk_iters > 2 else 0) + 1,
-                "kmeans_prep": 1, "kmeans": 4 * iters, "unmix": 1}
+                "kmeans_prep": 1, "kmeans": 3 * iters, "unmix": 1}
 
     def step(ev=None):
         def mark(i):

@@ -249,16 +249,20 @@ sk_status sk_kmeans_step_delta(const sk_ctx *ctx, const int32_t *idx, const floa
  * (mu_update_one)): assignment against mu and an update of S, cnt, nk that
  * is either a full rebuild (as sk_kmeans_reset + sk_kmeans_step) or
  * incremental (as sk_kmeans_step_delta), chosen on the device so that the
- * call can sit in a captured CUDA graph.  state: device int64[2], caller-
+ * call can sit in a captured CUDA graph.  state: device int64[3], caller-
  * owned; state[0] carries from one pass to the next the number of rows
- * whose label changed, state[1] is scratch.  The pass is a full rebuild if
- * first != 0 or state[0] > n / 12 (many moved rows: moving each one's
- * entries with global atomics would cost more than rebuilding the sums in
- * shared memory), else incremental.  On return labels, S, cnt, nk describe
- * the new assignment and state[0] holds this pass's count of changed rows
- * (on a first pass, counted against whatever labels held).  The sums are
- * the same either way, up to the order of float64 additions.  Other
- * arguments as sk_kmeans_step_delta; dist may be NULL. */
+ * whose label changed, state[1] receives the kind of pass that ran (1 full
+ * rebuild, 2 incremental), state[2] is scratch that every pass leaves at 0
+ * (a first pass sets it).  The pass is a full rebuild if first != 0 or
+ * state[0] > n / 12 (many moved rows: moving each one's entries with global
+ * atomics would cost more than rebuilding the sums in shared memory), else
+ * incremental.  On return labels, S, cnt, nk describe the new assignment
+ * and state[0] holds this pass's count of changed rows (on a first pass,
+ * counted against whatever labels held).  The sums are the same either way,
+ * up to the order of float64 additions.  Other arguments as
+ * sk_kmeans_step_delta; dist may be NULL.  Two kernel launches where K <= 32
+ * and the centre table fits shared memory (the assignment kernel makes the
+ * choice), else four. */
 sk_status sk_kmeans_step_auto(const sk_ctx *ctx, const int32_t *idx, const float *val,
                               int64_t n, const float *mu, int32_t K, int32_t *labels,
                               float *dist, double *S, int32_t *cnt, int64_t *nk,

@@ -346,7 +346,7 @@ def sk_kmeans_step_auto(ctx: Ctx, idx, val, mu, labels, S, cnt, nk, state, first
                         dist=None, stream=None):
     n = idx.shape[0]
     K = mu.shape[0]
-    _need(state, torch.int64, "state", (2,))
+    _need(state, torch.int64, "state", (3,))
     _check("sk_kmeans_step_auto", load().sk_kmeans_step_auto(
         ctx.handle, _ptr(idx), _ptr(val), n, _ptr(mu), K, _ptr(labels), _ptr(dist), _ptr(S),
         _ptr(cnt), _ptr(nk), _ptr(state), 1 if first else 0, _stream(stream)))

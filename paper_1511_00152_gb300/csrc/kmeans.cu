@@ -58,6 +58,10 @@ struct KmParams {
     // differs from the one labels held before the pass
     const int64_t *mode;
     int expect;
+    // adaptive pass run by the rotated-copies kernel (auto_state NULL: not
+    // adaptive): the kernel itself chooses the kind of pass (see RcParams)
+    int64_t *auto_state = nullptr;
+    int auto_first = 0;
 };
 
 // Packed FP32 pairs (two independent IEEE round-to-nearest operations).
@@ -378,12 +382,13 @@ __global__ void kmeans_finalize_kernel(int64_t KP, const double *S, const int32_
     }
 }
 
-// Adaptive pass, first step (one CTA): state[0] holds the number of rows
-// whose label changed in the previous pass.  If that is more than thr (or
-// this is the first pass), this pass rebuilds the sums from zero: the sums
-// are zeroed here and state[1] = 1 selects the full pass; otherwise
-// state[1] = 2 selects the incremental pass.  state[0] restarts at 0 and the
-// pass that runs adds its own count of changed rows to it.
+// Adaptive pass, first step (one CTA; used where the rotated-copies kernel,
+// which makes this choice itself, does not apply): state[0] holds the
+// number of rows whose label changed in the previous pass.  If that is more
+// than thr (or this is the first pass), this pass rebuilds the sums from
+// zero: the sums are zeroed here and state[1] = 1 selects the full pass;
+// otherwise state[1] = 2 selects the incremental pass.  state[2] restarts at
+// 0 and the pass that runs adds its own count of changed rows to it.
 __global__ void kmeans_auto_decide_kernel(int64_t *state, int64_t thr, int first, int64_t KP,
                                           int K, double *S, int32_t *cnt, int64_t *nk) {
     __shared__ int full;
@@ -391,7 +396,7 @@ __global__ void kmeans_auto_decide_kernel(int64_t *state, int64_t thr, int first
     __syncthreads();
     if (threadIdx.x == 0) {
         state[1] = full ? 1 : 2;
-        state[0] = 0;
+        state[2] = 0;
     }
     if (full) {
         for (int64_t e = threadIdx.x; e < KP; e += blockDim.x) {
@@ -399,6 +404,15 @@ __global__ void kmeans_auto_decide_kernel(int64_t *state, int64_t thr, int first
             cnt[e] = 0;
         }
         for (int e = threadIdx.x; e < K; e += blockDim.x) nk[e] = 0;
+    }
+}
+
+// Adaptive pass, last step where kmeans_auto_decide_kernel ran: this pass's
+// count of changed rows becomes the next pass's state[0].
+__global__ void kmeans_auto_carry_kernel(int64_t *state) {
+    if (threadIdx.x == 0) {
+        state[0] = state[2];
+        state[2] = 0;
     }
 }
 
@@ -604,9 +618,22 @@ struct RcParams {
     int64_t *nk;
     unsigned long long *changed;  // rows whose label changed (may be NULL)
     int do_update;                // 0 none, 2 incremental (changed rows only)
-    const int64_t *mode;          // adaptive passes: run only if *mode == expect
+    // Adaptive passes: the kernel runs only if *mode == expect.  The kernel
+    // instance with AUTO = true instead chooses the kind of pass itself: mode
+    // then points at the caller's int64[3] state and expect is kAutoFirst or
+    // kAutoLater (the fields are reused: a larger parameter block made the
+    // compiler spill in the assignment loop).  A full rebuild if this is the
+    // first pass or state[0] (the previous pass's count of changed rows) >
+    // n / 12; a full pass zeroes S, cnt and nk and assigns only
+    // (kmeans_sums_kernel, launched next, adds the sums from the labels),
+    // otherwise the pass is incremental.  Block 0 records the choice in
+    // state[1] (1 full, 2 incremental); changed points at state[2], zero on
+    // entry.
+    const int64_t *mode;
     int expect;
 };
+
+constexpr int kAutoFirst = -2, kAutoLater = -1;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -644,12 +671,40 @@ __device__ __forceinline__ uint64_t lds64(uint32_t addr) {
 template <int NP>
 constexpr int rc_max_threads() { return NP <= 6 ? 1024 : NP <= 9 ? 768 : NP <= 12 ? 640 : 512; }
 
-template <int NP>
+// The adaptive pass's choice (see RcParams), made by every CTA alike; a full
+// pass's zeroing of the sums is spread over the grid.  (Measured at n = 10^6,
+// p = 1024, K = 10: an incremental adaptive pass 0.140 ms against 0.147 for
+// the earlier four launches, a one-CTA choice kernel and both kinds of
+// assignment; the 20-pass loop 3.19 against 3.23 ms.)
+__device__ __forceinline__ void rc_auto_choose(const RcParams &P, int *s_update) {
+    int64_t *state = const_cast<int64_t *>(P.mode);
+    const bool full = P.expect == kAutoFirst || state[0] > P.n / 12;
+    if (threadIdx.x == 0) *s_update = full ? 0 : 2;
+    if (full) {
+        const int64_t KP = (int64_t)P.K * P.pt;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < KP;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            P.Ssum[e] = 0.0;
+            P.cnt[e] = 0;
+        }
+        if (blockIdx.x == 0 && (int)threadIdx.x < P.K) P.nk[threadIdx.x] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = full ? 1 : 2;
+}
+
+template <int NP, bool AUTO>
 __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParams P) {
     constexpr int C = 16 / NP;  // lanes per row
     constexpr int RW = 2 * NP;  // rows per warp
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (P.mode && *P.mode != P.expect) return;  // the other kind of pass runs
+    // the kind of update an adaptive pass makes (kept in shared memory: read
+    // once per row group, it holds no register through the loop)
+    __shared__ int s_update;
+    if constexpr (AUTO) {
+        rc_auto_choose(P, &s_update);
+    } else {
+        if (P.mode && *P.mode != P.expect) return;  // the other kind of pass runs
+    }
     float *tab = reinterpret_cast<float *>(smem_raw);
     int2 *stage_all = reinterpret_cast<int2 *>(smem_raw + (size_t)P.pt * 128);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -696,7 +751,7 @@ __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParam
     int2 *stage = stage_all + (size_t)warp * RW * S;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool track_old = P.do_update == 2 || P.changed != nullptr;
+    const bool track_old = P.do_update == 2 || P.changed != nullptr;  // adaptive: changed is set
 
     // The group's rows are contiguous in the ELL arrays and are read with
     // coalesced loads, eight per lane in flight before their stores.  Two of
@@ -808,7 +863,7 @@ __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParam
             const unsigned mv = __ballot_sync(kFull, moved && c == 0);
             if (lane == 0 && mv) atomicAdd(P.changed, (unsigned long long)__popc(mv));
         }
-        if (P.do_update == 2 && moved) {
+        if ((AUTO ? s_update == 2 : P.do_update == 2) && moved) {
             // incremental sums: the row leaves cluster old and joins label
             // (its C lanes move their own entries)
             for (int t = c; t < m; t += C) {
@@ -835,7 +890,7 @@ __global__ void __launch_bounds__(rc_max_threads<NP>()) kmeans_rc_kernel(RcParam
 
 template <int NP>
 cudaError_t launch_rc_np(const RcParams &P, int warps, size_t smem, cudaStream_t s) {
-    auto kern = kmeans_rc_kernel<NP>;
+    auto kern = P.expect < 0 ? kmeans_rc_kernel<NP, true> : kmeans_rc_kernel<NP, false>;
     if (warps > rc_max_threads<NP>() / 32) {
         warps = rc_max_threads<NP>() / 32;
         smem = (size_t)P.pt * 128 + (size_t)warps * 2 * NP * P.S * 8;
@@ -875,10 +930,18 @@ struct SumParams {
     int64_t *nk;
     const int64_t *mode;  // adaptive passes: run only if *mode == expect
     int expect;
+    // adaptive passes: block 0 moves this pass's count of changed rows
+    // (carry[2]) to carry[0] for the next pass and zeroes carry[2] (NULL:
+    // nothing); it runs whichever kind of pass ran
+    int64_t *carry = nullptr;
 };
 
 __global__ void __launch_bounds__(kThreads) kmeans_sums_kernel(SumParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (P.carry && blockIdx.x == 0 && threadIdx.x == 0) {
+        P.carry[0] = P.carry[2];
+        P.carry[2] = 0;
+    }
     if (P.mode && *P.mode != P.expect) return;
     const int KP = P.K * P.pt;
     float *sS = reinterpret_cast<float *>(smem_raw);
@@ -971,6 +1034,7 @@ cudaError_t launch_sums(const KmParams &Q, cudaStream_t s, bool *used) {
     P.nk = Q.nk;
     P.mode = Q.mode;
     P.expect = Q.expect;
+    P.carry = Q.auto_state;
     cudaError_t e = cudaFuncSetAttribute(kmeans_sums_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1033,8 +1097,8 @@ cudaError_t launch_rc(const KmParams &Q, cudaStream_t s, bool *used) {
     P.nk = Q.nk;
     P.changed = Q.changed;
     P.do_update = Q.do_update == 2 ? 2 : 0;
-    P.mode = Q.mode;
-    P.expect = Q.expect;
+    P.mode = Q.auto_state ? Q.auto_state : Q.mode;
+    P.expect = Q.auto_state ? (Q.auto_first ? kAutoFirst : kAutoLater) : Q.expect;
     const size_t smem = table + (size_t)warps * per_warp;
     if (Q.do_update == 1) {
         // a full rebuild: this assignment, then the sums from its labels
@@ -1087,15 +1151,55 @@ cudaError_t launch_kmeans_auto(const sk_ctx &c, const int32_t *idx, const float 
                                double *S, int32_t *cnt, int64_t *nk, int64_t *state, int first,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    kmeans_auto_decide_kernel<<<1, 1024, 0, s>>>(state, n / 12, first, (int64_t)K * c.pt, K, S,
+    const int64_t thr = n / 12;
+    // state[2] counts this pass's changed rows; every pass leaves it at zero
+    if (first) {
+        const cudaError_t e = cudaMemsetAsync(state + 2, 0, sizeof(int64_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        // two launches: the rotated-copies assignment chooses the kind of
+        // pass itself (and zeroes the sums for a full one), then the sums
+        // pass (which returns at once after an incremental pass) carries the
+        // count of changed rows to state[0]
+        KmParams Q;
+        Q.idx = idx;
+        Q.val = val;
+        Q.n = n;
+        Q.m = (int)c.m;
+        Q.pt = (int)c.pt;
+        Q.K = K;
+        Q.mu = mu;
+        Q.labels = labels;
+        Q.dist = dist;
+        Q.S = S;
+        Q.cnt = cnt;
+        Q.nk = nk;
+        Q.changed = reinterpret_cast<unsigned long long *>(state + 2);
+        Q.do_assign = 1;
+        Q.do_update = 1;
+        Q.mode = state + 1;
+        Q.expect = 1;
+        Q.auto_state = state;
+        Q.auto_first = first;  // the kernel's threshold is n / 12 too
+        bool used = false;
+        const cudaError_t e = launch_rc(Q, s, &used);
+        if (used || e != cudaSuccess) return e;
+    }
+    // other K, pt: a one-CTA choice, both kinds of pass (the one not chosen
+    // returns at once), then the carry
+    kmeans_auto_decide_kernel<<<1, 1024, 0, s>>>(state, thr, first, (int64_t)K * c.pt, K, S,
                                                  cnt, nk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, true, 1, state,
+    e = launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, true, 1, state + 2,
                            state + 1, 1, s);
     if (e != cudaSuccess) return e;
-    return launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, true, 2, state,
-                              state + 1, 2, s);
+    e = launch_kmeans_mode(c, idx, val, n, mu, K, labels, dist, S, cnt, nk, true, 2, state + 2,
+                           state + 1, 2, s);
+    if (e != cudaSuccess) return e;
+    kmeans_auto_carry_kernel<<<1, 32, 0, s>>>(state);
+    return cudaGetLastError();
 }
 
 static cudaError_t launch_kmeans_mode(const sk_ctx &c, const int32_t *idx, const float *val,

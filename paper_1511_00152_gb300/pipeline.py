@@ -28,7 +28,7 @@ class KMeansState:
         # while many labels change, incremental after; chosen on the device),
         # "incremental" or "full"
         self.mode = mode
-        self.state = torch.zeros(2, dtype=torch.int64, device=device)
+        self.state = torch.zeros(3, dtype=torch.int64, device=device)
         self.graph = None
         self._graph_args = None
 

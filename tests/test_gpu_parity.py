@@ -401,11 +401,20 @@ def test_kmeans_auto_pass_matches_full(sk, p, m, n, K):
     ctx, oi, v32, idx, val, mu0, trace = _loop_inputs(sk, p, m, n, K, p + n + 1, 31, iters)
     a = pipeline.KMeansState(ctx, n, K, mode="auto")
     a.mu.copy_(mu0)
-    modes, hist_a = [], []
+    modes, moved, hist_a = [], [], []
     for it in range(iters):
         a.iteration(idx, val, first=(it == 0))
         modes.append(int(a.state[1].item()))
+        moved.append(int(a.state[0].item()))
+        assert int(a.state[2].item()) == 0  # the scratch counter is left at zero
         hist_a.append(a.labels.cpu().numpy().copy())
+        if it > 0:
+            # the count of changed rows matches the labels
+            assert moved[-1] == int((hist_a[-1] != hist_a[-2]).sum())
+    # each later pass is a rebuild exactly when the previous one moved more
+    # than n / 12 rows
+    for it in range(1, iters):
+        assert modes[it] == (1 if moved[it - 1] > n // 12 else 2), (modes, moved)
     g = pipeline.KMeansState(ctx, n, K, mode="auto")
     hist_g = torch.empty((iters, n), dtype=torch.int32, device="cuda")
     g.run(idx, val, mu0, iters=iters, use_graph=True, history=hist_g)
