@@ -22,6 +22,8 @@
 #include <cstring>
 #include <vector>
 
+#include <type_traits>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -199,10 +201,36 @@ __device__ __forceinline__ void wht_stage(uint64_t (&w)[NPAIR], int rb) {
     }
 }
 
-__device__ __forceinline__ int readA(const uint32_t *A, uint32_t tag, int j) {
-    const uint32_t a = A[j];
-    return (a >> 16) == tag ? (int)(a & 0xFFFFu) : j;
-}
+// Entries of the virtual Fisher-Yates array: the value a position holds and
+// the tag of the row that wrote it; a position whose tag is not the current
+// row's still holds its own index.  32-bit entries: 16-bit tag and value.
+// 16-bit entries (the masks-alone kernel, L <= 13): an L-bit value and a
+// (16 - L)-bit tag, so the array is cleared every kTagMax rows.
+template <typename AT, int L>
+struct AEnt;
+template <int L>
+struct AEnt<uint32_t, L> {
+    static constexpr uint32_t kTagMax = 0xFFFFu;
+    __device__ static int read(const uint32_t *A, uint32_t tag, int j) {
+        const uint32_t a = A[j];
+        return (a >> 16) == tag ? (int)(a & 0xFFFFu) : j;
+    }
+    __device__ static void write(uint32_t *A, int k, uint32_t tag, int V) {
+        A[k] = (tag << 16) | (uint32_t)V;
+    }
+};
+template <int L>
+struct AEnt<uint16_t, L> {
+    static_assert(L <= 13, "16-bit entries leave at least three tag bits");
+    static constexpr uint32_t kTagMax = (1u << (16 - L)) - 1u;
+    __device__ static int read(const uint16_t *A, uint32_t tag, int j) {
+        const uint32_t a = A[j];
+        return (a >> L) == tag ? (int)(a & ((1u << L) - 1u)) : j;
+    }
+    __device__ static void write(uint16_t *A, int k, uint32_t tag, int V) {
+        A[k] = (uint16_t)((tag << L) | (uint32_t)V);
+    }
+};
 
 // Window of the row's mask-word stream: two batches of 128 words (one
 // Philox block per lane per batch), batch b in slot b & 1.
@@ -227,9 +255,9 @@ __device__ __forceinline__ void ensure_batches(WordWindow &ww, const CompressPar
 }
 
 // Mask of one row and (GATHER) its ELL gather, by one warp.
-template <int L, bool GATHER = true>
+template <int L, bool GATHER = true, typename AT = uint32_t>
 __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
-                                           const float *ybuf, int ebase, uint32_t *A,
+                                           const float *ybuf, int ebase, AT *A,
                                            uint32_t *hit, uint32_t *words, uint32_t tag, int lane) {
     // the range [0, PT) of the draw: 2^L, or (masks alone) p <= 2^L for the DCT
     const int PT = GATHER ? (1 << L) : P.mask_pt;
@@ -298,7 +326,7 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
         const int src = srcm ? 31 - __clz(srcm) : lane;
         // a row's first chunk finds every position still holding its own
         // index (the mask kernel skips that look-up)
-        const int vbase = act ? ((GATHER || c0) ? readA(A, tag, t) : t) : 0;
+        const int vbase = act ? ((GATHER || c0) ? AEnt<AT, L>::read(A, tag, t) : t) : 0;
         int V = vbase;  // value at position t just before step t
         for (;;) {
             const int from = __shfl_sync(kFull, V, src);
@@ -311,10 +339,10 @@ __device__ __forceinline__ void sample_row(const CompressParams &P, int64_t i,
         const int prev = prevm ? 31 - __clz(prevm) : lane;
         const int vprev = __shfl_sync(kFull, V, prev);
         int omega = 0;
-        if (act) omega = prevm ? vprev : ((GATHER || c0) ? readA(A, tag, k) : k);
+        if (act) omega = prevm ? vprev : ((GATHER || c0) ? AEnt<AT, L>::read(A, tag, k) : k);
         __syncwarp();
         if (act && c0 + 32 < m && (grpm & gt) == 0u && k >= c0 + 32)
-            A[k] = (tag << 16) | (uint32_t)V;
+            AEnt<AT, L>::write(A, k, tag, V);
         if (act) {
             oidx[t] = omega;
             if constexpr (GATHER) oval[t] = ybuf[yaddr<L>(ebase, omega)] * P.scale;
@@ -633,9 +661,14 @@ __global__ void __launch_bounds__(kWarps * 32, 2) compress_kernel(CompressParams
 template <int L>
 __host__ __device__ constexpr int mask_warps() { return L >= 13 ? 2 : 4; }
 
+// the masks-alone kernel's virtual Fisher-Yates entries: 16 bits while a
+// position fits 13 bits (half the shared memory per warp, twice the warps)
+template <int L>
+using MaskAT = typename std::conditional<(L <= 13), uint16_t, uint32_t>::type;
+
 template <int L>
 constexpr size_t mask_smem_bytes() {
-    return (size_t)mask_warps<L>() * (256 * 4 + (1 << L) * 4 + 32 * 4);
+    return (size_t)mask_warps<L>() * (256 * 4 + (1 << L) * sizeof(MaskAT<L>) + 32 * 4);
 }
 
 template <int L>
@@ -644,17 +677,19 @@ __global__ void __launch_bounds__(mask_warps<L>() * 32) mask_kernel(CompressPara
     constexpr int MW = mask_warps<L>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    using AT = MaskAT<L>;
     uint32_t *words = reinterpret_cast<uint32_t *>(smem_raw) + warp * 256;
-    uint32_t *A = reinterpret_cast<uint32_t *>(smem_raw + (size_t)MW * 256 * 4) + warp * PT;
-    uint32_t *hit =
-        reinterpret_cast<uint32_t *>(smem_raw + (size_t)MW * (256 * 4 + PT * 4)) + warp * 32;
-    for (int j = lane; j < PT; j += 32) A[j] = 0u;
+    AT *A = reinterpret_cast<AT *>(smem_raw + (size_t)MW * 256 * 4) + warp * PT;
+    uint32_t *hit = reinterpret_cast<uint32_t *>(smem_raw + (size_t)MW * (256 * 4 + PT * sizeof(AT))) +
+                    warp * 32;
+    for (int j = lane; j < PT; j += 32) A[j] = 0;
     __syncwarp();
     uint32_t tag = 1;
     for (int64_t i = (int64_t)blockIdx.x * MW + warp; i < P.n; i += (int64_t)gridDim.x * MW) {
-        sample_row<L, false>(P, i, nullptr, 0, A, hit, words, tag, lane);
-        if (++tag == 0x10000u) {
-            for (int j = lane; j < PT; j += 32) A[j] = 0u;
+        sample_row<L, false, AT>(P, i, nullptr, 0, A, hit, words, tag, lane);
+        if (++tag > AEnt<AT, L>::kTagMax) {
+            __syncwarp();
+            for (int j = lane; j < PT; j += 32) A[j] = 0;
             __syncwarp();
             tag = 1;
         }
