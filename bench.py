@@ -61,10 +61,11 @@ UNIT = "samples/s"
 # dominant kernel from one ncu capture of this workload, valid only while the
 # kernel source still has the digest it had when captured.
 KERNEL_TRAFFIC = {
-    # kmeans_rc_kernel: 164.87 MB read + 3.88 MB written per incremental pass
-    # at n = 400,000 (421.9 B per row), scaled to n = 10^6
-    "kmeans": {"bytes": 421_900_000, "n": 1_000_000, "p": 1024,
-               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "d2f00a6be855b224"},
+    # kmeans_rc_kernel<5, 1> (adaptive pass, incremental): 164.88 MB read +
+    # 4.19 MB written per launch at n = 400,000 (422.7 B per row), scaled to
+    # n = 10^6
+    "kmeans": {"bytes": 422_700_000, "n": 1_000_000, "p": 1024,
+               "source": "paper_1511_00152_gb300/csrc/kmeans.cu", "src_sha": "e3f68cf3451fcfb0"},
     # gram_tc_kernel (split-BF16): 178.28 MB read + 9.86 MB written per launch
     # at n = 400,000; the reads (the ELL rows, read once from DRAM by all of a
     # row range's tiles) scaled to n = 10^6, the writes (the float64 Gram's
