@@ -437,28 +437,59 @@ __global__ void __launch_bounds__(kWarpRowsWarps * 32, 2) dct_forward_warp_kerne
                 }
             }
         }
+        // this row's sampled coordinates (the first kMI per lane), fetched
+        // before the transform so that their latency hides behind it
+        constexpr int kMI = 4;
+        int jv[kMI];
+        if constexpr (!DENSE) {
+            const int32_t *gi = P.idx + i * P.m;
+#pragma unroll
+            for (int u = 0; u < kMI; ++u) {
+                const int t = lane + 32 * u;
+                jv[u] = t < P.m ? __ldcg(gi + t) : 0;
+            }
+        }
         load_row(i + nw);
         __syncwarp();
         float2 *Z = fft<float2, Twiddle<float, true>, true>(b0, b1, P, twf, lane, 32);
-        float *y = reinterpret_cast<float *>(Z == b0 ? b1 : b0);
-        for (int k = lane; k <= L; k += 32) {
+        // coefficient k of the post-twiddle gives outputs k (its real part)
+        // and N - k (its imaginary part, 0 < k < L)
+        auto post = [&](int k) -> float2 {
             const float2 Zk = Z[k == L ? 0 : k];
             const float2 Zc = cconj(Z[k == 0 ? 0 : L - k]);
             const float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
             const float2 O = make_float2(0.5f * (Zk.y - Zc.y), -0.5f * (Zk.x - Zc.x));
             const float2 V = cadd(E, cmul(om[k], O));
-            const float2 W = cmul(ph[k], V);
-            if (k < N) y[k] = (k == 0 ? s0 : s1) * W.x;
-            if (k > 0 && k < L) y[N - k] = s1 * (-W.y);
-        }
-        __syncwarp();
+            return cmul(ph[k], V);
+        };
         if constexpr (DENSE) {
+            float *y = reinterpret_cast<float *>(Z == b0 ? b1 : b0);
+            for (int k = lane; k <= L; k += 32) {
+                const float2 W = post(k);
+                if (k < N) y[k] = (k == 0 ? s0 : s1) * W.x;
+                if (k > 0 && k < L) y[N - k] = s1 * (-W.y);
+            }
+            __syncwarp();
             float *Y = static_cast<float *>(P.out) + i * N;
             for (int k = lane; k < N; k += 32) Y[k] = y[k];
         } else {
+            // only the m sampled outputs: output j comes from coefficient
+            // j (j <= L) or N - j (j > L), the same arithmetic as the dense
+            // form
             const int32_t *gi = P.idx + i * P.m;
             float *ov = P.val + i * P.m;
-            for (int t = lane; t < P.m; t += 32) ov[t] = y[clamp_index(__ldcg(gi + t), N)];
+            auto out1 = [&](int t, int jraw) {
+                const int j = clamp_index(jraw, N);
+                const int k = j <= L ? j : N - j;
+                const float2 W = post(k);
+                ov[t] = j <= L ? (j == 0 ? s0 : s1) * W.x : s1 * (-W.y);
+            };
+#pragma unroll
+            for (int u = 0; u < kMI; ++u) {
+                const int t = lane + 32 * u;
+                if (t < P.m) out1(t, jv[u]);
+            }
+            for (int t = lane + 32 * kMI; t < P.m; t += 32) out1(t, __ldcg(gi + t));
         }
         __syncwarp();
     }
