@@ -28,6 +28,8 @@
 // float32 or float64.
 #include <cstring>
 
+#include <algorithm>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -596,6 +598,57 @@ cudaError_t launch_rows(K kern, const DctParams &P, size_t smem, cudaStream_t s)
 
 // The radices of L = p / 2 in stage order (8, 4, 2 first, then odd primes up
 // to 13); false if L has a prime factor above 13.
+// Shared-memory wavefronts of the warp kernel's FFT stages in the order
+// fac[0..nf) (a cost model, no launch): a warp's threads take butterflies
+// j = lane, lane + 32, ...; each load in[j + r S], twiddle tw(k r st) and
+// store out[(j / Ns) Ns R + k + q Ns] moves 8 bytes a lane, served a
+// half-warp at a time, each half-warp taking as many wavefronts as the most
+// distinct 4-byte words any one of the 32 banks holds.
+static int64_t dct_stage_cost(int64_t L, const int *fac, int nf) {
+    auto wavefronts = [](const int64_t *e, int cnt) -> int64_t {
+        // e: 8-byte element indices of the active lanes of one half-warp
+        if (cnt == 0) return 0;
+        int64_t words[32];
+        int nw = 0;
+        for (int i = 0; i < cnt; ++i)
+            for (int h = 0; h < 2; ++h) {
+                const int64_t w = 2 * e[i] + h;
+                bool seen = false;
+                for (int q = 0; q < nw; ++q) seen = seen || words[q] == w;
+                if (!seen) words[nw++] = w;
+            }
+        int per_bank[32] = {0};
+        int most = 0;
+        for (int q = 0; q < nw; ++q) {
+            const int b = (int)(words[q] & 31);
+            if (++per_bank[b] > most) most = per_bank[b];
+        }
+        return most;
+    };
+    int64_t cost = 0, Ns = 1;
+    for (int s = 0; s < nf; ++s) {
+        const int64_t R = fac[s], S = L / R, st = L / (Ns * R);
+        for (int64_t t0 = 0; t0 < S; t0 += 32)
+            for (int64_t r = 0; r < R; ++r)
+                for (int kind = 0; kind < 3; ++kind) {
+                    if (kind == 2 && (Ns == 1 || r == 0)) continue;  // no twiddle
+                    for (int half = 0; half < 2; ++half) {
+                        int64_t e[16];
+                        int cnt = 0;
+                        for (int64_t j = t0 + 16 * half; j < t0 + 16 * half + 16 && j < S; ++j) {
+                            const int64_t jq = j / Ns, k = j - jq * Ns;
+                            e[cnt++] = kind == 0 ? j + r * S
+                                     : kind == 1 ? jq * Ns * R + k + r * Ns
+                                                 : (k * r * st) % L;
+                        }
+                        cost += wavefronts(e, cnt);
+                    }
+                }
+        Ns *= R;
+    }
+    return cost;
+}
+
 bool dct_factor(int64_t L, int *fac, int *nf) {
     int k = 0;
     while (L > 1 && L % 8 == 0 && k < 16) {
@@ -610,13 +663,54 @@ bool dct_factor(int64_t L, int *fac, int *nf) {
         fac[k++] = 2;
         L /= 2;
     }
+    const int64_t L0 = [&] {
+        int64_t v = L;
+        for (int q = 0; q < k; ++q) v *= fac[q];
+        return v;
+    }();
     for (int r : {3, 5, 7, 11, 13})
         while (L > 1 && L % r == 0 && k < 16) {
             fac[k++] = r;
             L /= r;
         }
     *nf = k;
-    return L == 1;
+    if (L != 1) return false;
+    // Stage order: any order gives the same transform (up to rounding); the
+    // one the cost model above rates cheapest is kept (ties: the first
+    // met).  Candidates: every distinct order of up to six stages, else the
+    // radices-2^k-first order and that order with each distinct radix moved
+    // to the front.  (L = 392 = 8 7 7: a first radix-8 stage stores at a
+    // stride of 8 elements, 16 lanes into 2 banks; radix 7 first stores at
+    // an odd stride, one wavefront per half-warp.)
+    int best[16];
+    for (int q = 0; q < k; ++q) best[q] = fac[q];
+    int64_t best_cost = dct_stage_cost(L0, best, k);
+    auto consider = [&](const int *cand) {
+        const int64_t c = dct_stage_cost(L0, cand, k);
+        if (c < best_cost) {
+            best_cost = c;
+            for (int q = 0; q < k; ++q) best[q] = cand[q];
+        }
+    };
+    if (k <= 6) {
+        int cand[16];
+        for (int q = 0; q < k; ++q) cand[q] = fac[q];
+        std::sort(cand, cand + k);
+        do consider(cand);
+        while (std::next_permutation(cand, cand + k));
+    } else {
+        for (int q = 1; q < k; ++q) {
+            if (fac[q] == fac[q - 1]) continue;
+            int cand[16];
+            cand[0] = fac[q];
+            int w = 1;
+            for (int u = 0; u < k; ++u)
+                if (u != q) cand[w++] = fac[u];
+            consider(cand);
+        }
+    }
+    for (int q = 0; q < k; ++q) fac[q] = best[q];
+    return true;
 }
 
 size_t dct_forward_smem(const sk_ctx &c) {

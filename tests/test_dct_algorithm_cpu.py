@@ -8,7 +8,13 @@ mixed-radix FFT with the kernel's stage addressing (input j + r S, twiddle
 index k r st, output (j / Ns) Ns R + k + q Ns) and its butterflies (radix
 2, 4 and 8 written out, odd radices in the symmetric form), then E, O, V, W and
 X_k = Re W_k, X_{N-k} = -Im W_k.  Inverse: the same steps backwards with the
-inverse FFT, as the un-mixing kernel runs them."""
+inverse FFT, as the un-mixing kernel runs them.
+
+The library runs the stages in the order its shared-memory cost model rates
+cheapest for the length; every distinct order of the radices is checked
+here, so whichever it picks is covered."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -16,7 +22,8 @@ scipy_fft = pytest.importorskip("scipy.fft")
 
 
 def factor(L):
-    """The kernels' stage order: 8, 4, 2 first, then odd primes up to 13."""
+    """The kernels' radices, 8, 4, 2 first, then odd primes up to 13 (the
+    library may run them in another order)."""
     out = []
     for r in (8, 4, 2):
         while L > 1 and L % r == 0:
@@ -61,11 +68,16 @@ def butterfly(x, R, d, rt):
     return y
 
 
-def fft_stockham(z, direction):
+def orders(L, cap=60):
+    """Distinct orders of factor(L) (at most cap of them)."""
+    return list(itertools.islice(sorted(set(itertools.permutations(factor(L)))), cap))
+
+
+def fft_stockham(z, direction, order=None):
     L = len(z)
     tw = np.exp(-direction * 2j * np.pi * np.arange(L) / L)
     a, Ns = z.astype(np.complex128).copy(), 1
-    for R in factor(L):
+    for R in (factor(L) if order is None else order):
         S, st = L // R, L // (Ns * R)
         b = np.empty_like(a)
         rt = tw[np.arange(R) * S]
@@ -82,12 +94,12 @@ def fft_stockham(z, direction):
     return a
 
 
-def dct2(x):
+def dct2(x, order=None):
     N = len(x)
     L = N // 2
     v = np.empty(N)
     v[:L], v[N - 1 - np.arange(L)] = x[0::2], x[1::2]
-    Z = fft_stockham(v[0::2] + 1j * v[1::2], 1)
+    Z = fft_stockham(v[0::2] + 1j * v[1::2], 1, order)
     y = np.empty(N)
     s = np.full(N, np.sqrt(2 / N))
     s[0] = np.sqrt(1 / N)
@@ -101,7 +113,7 @@ def dct2(x):
     return y
 
 
-def dct3(y):
+def dct3(y, order=None):
     N = len(y)
     L = N // 2
     s = np.full(N, np.sqrt(2 / N))
@@ -116,7 +128,7 @@ def dct3(y):
         E = (V[k] + np.conj(V[L - k])) / 2
         D = (V[k] - np.conj(V[L - k])) / 2
         Z[k] = E + 1j * D * np.exp(2j * np.pi * k / N)
-    z = fft_stockham(Z, -1) / L
+    z = fft_stockham(Z, -1, order) / L
     v = np.empty(N)
     v[0::2], v[1::2] = z.real, z.imag
     x = np.empty(N)
@@ -132,8 +144,19 @@ def test_kernel_dct_arithmetic_matches_scipy(N):
     assert np.max(np.abs(dct3(x) - scipy_fft.dct(x, type=3, norm="ortho"))) < 1e-11
 
 
-@pytest.mark.parametrize("L", [8, 12, 49, 125, 143, 392, 1001])
+@pytest.mark.parametrize("L", [8, 12, 49, 98, 125, 143, 200, 392, 500, 1001])
 def test_kernel_fft_stage_addressing(L):
     z = np.random.default_rng(L).standard_normal(L) + 1j * np.random.default_rng(L + 1).standard_normal(L)
-    assert np.max(np.abs(fft_stockham(z, 1) - np.fft.fft(z))) < 1e-10
-    assert np.max(np.abs(fft_stockham(z, -1) - L * np.fft.ifft(z))) < 1e-10
+    for order in orders(L):
+        assert np.max(np.abs(fft_stockham(z, 1, order) - np.fft.fft(z))) < 1e-10, order
+        assert np.max(np.abs(fft_stockham(z, -1, order) - L * np.fft.ifft(z))) < 1e-10, order
+
+
+@pytest.mark.parametrize("N", [200, 784, 1000, 2 * 1001])
+def test_kernel_dct_every_stage_order(N):
+    x = np.random.default_rng(N + 7).standard_normal(N)
+    ref2 = scipy_fft.dct(x, type=2, norm="ortho")
+    ref3 = scipy_fft.dct(x, type=3, norm="ortho")
+    for order in orders(N // 2):
+        assert np.max(np.abs(dct2(x, order) - ref2)) < 1e-11, order
+        assert np.max(np.abs(dct3(x, order) - ref3)) < 1e-11, order
