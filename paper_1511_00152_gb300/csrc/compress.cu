@@ -443,8 +443,22 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
                           smem_u32(mbar + b0), lane);
         }
     }
+    // SPLIT: the first kMI of this lane's sampled coordinates of the row,
+    // fetched before its transform so that their latency hides behind it
+    constexpr int kMI = SPLIT ? 2 : 1;
     for (int64_t u = u_first; u < nunits; u += stride, ++kloc) {
         const int64_t r0 = u * RPU;
+        int jv[kMI];
+        if constexpr (SPLIT) {
+            if (r0 < P.n) {
+                const int32_t *gi = P.idx + r0 * (int64_t)P.m;
+#pragma unroll
+                for (int q = 0; q < kMI; ++q) {
+                    const int t = wg * 32 + lane + q * G * 32;
+                    jv[q] = t < P.m ? __ldcg(gi + t) : 0;
+                }
+            }
+        }
         float v[32];
         if constexpr (TMA) {
             const int bsel = (int)(kloc & 1);
@@ -617,7 +631,12 @@ __device__ __forceinline__ bool compress_units(const CompressParams &P, int64_t 
                 const int m = P.m;
                 const int32_t *gi = P.idx + r0 * (int64_t)m;
                 float *ov = P.val + r0 * (int64_t)m;
-                for (int t = wg * 32 + lane; t < m; t += G * 32)
+#pragma unroll
+                for (int q = 0; q < kMI; ++q) {
+                    const int t = wg * 32 + lane + q * G * 32;
+                    if (t < m) ov[t] = ybuf[yaddr<L>(0, jv[q] & (PT - 1))] * P.scale;
+                }
+                for (int t = wg * 32 + lane + kMI * G * 32; t < m; t += G * 32)
                     ov[t] = ybuf[yaddr<L>(0, __ldcg(gi + t) & (PT - 1))] * P.scale;
             }
         } else {
