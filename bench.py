@@ -1050,7 +1050,9 @@ def run_batching(args, standalone=True):
                      "compress_bytes": comp_b, "kmeans_bytes": km_b, "gram_flops": flops,
                      "peak_hbm_gbs": hbm, "peak_bf16_tflops": bf16s, "peak_source": src},
         "clocks": clocks,
-        "gpu_launches_per_step": 1 + 2 + len(shapes) + 1 + 2 * iters,
+        # per K-means iteration: the pass (one launch for the data sets whose
+        # centre table fits shared memory, one for the others) and the finalize
+        "gpu_launches_per_step": 1 + 2 + len(shapes) + 1 + 3 * iters,
     }
     del br, ds
     if not standalone:

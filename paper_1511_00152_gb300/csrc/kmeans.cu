@@ -1298,12 +1298,19 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
         }
     }
     start[nd] = total;
-    // costliest rows (m K) first
+    // tasks whose centre table stays in shared memory (or is not needed)
+    // first, then those reading it from global memory; within each group
+    // the costliest rows (m K) first
     std::stable_sort(tasks.begin(), tasks.end(), [&](const KmTask &a, const KmTask &b) {
+        const int ga = (a.variant & 4) ? 1 : 0, gb = (b.variant & 4) ? 1 : 0;
+        if (ga != gb) return ga < gb;
         return (int64_t)Ps[a.d].m * Ps[a.d].K > (int64_t)Ps[b.d].m * Ps[b.d].K;
     });
     info.nd = nd;
     info.ntasks = (int)tasks.size();
+    info.ntasks_smem = 0;
+    while (info.ntasks_smem < info.ntasks && !(tasks[info.ntasks_smem].variant & 4))
+        ++info.ntasks_smem;
     info.total = total;
     info.mu_cap = (int)mu_cap;
     info.smem = mu_cap + stage_used;
@@ -1311,7 +1318,7 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
     info.tasks_off = km_al256(info.params_off + Ps.size() * sizeof(KmParams));
     info.start_off = km_al256(info.tasks_off + tasks.size() * sizeof(KmTask));
     info.ticket_off = km_al256(info.start_off + start.size() * sizeof(int64_t));
-    table.resize(info.ticket_off + 256, 0);
+    table.resize(info.ticket_off + 256, 0);  // two tickets: one per launch
     std::memcpy(table.data() + info.params_off, Ps.data(), Ps.size() * sizeof(KmParams));
     if (!tasks.empty())
         std::memcpy(table.data() + info.tasks_off, tasks.data(), tasks.size() * sizeof(KmTask));
@@ -1325,8 +1332,18 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
                                                   info.smem);
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sms * per_sm;
-    if (grid > info.ntasks) grid = info.ntasks > 0 ? info.ntasks : 1;
+    const int na = info.ntasks_smem, ng = info.ntasks - info.ntasks_smem;
+    if (grid > na) grid = na > 0 ? na : 1;
     info.grid = (int)grid;
+    // the global-table launch: staging only
+    info.smem_g = stage_used;
+    per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeans_batch_kernel, kThreads,
+                                                  info.smem_g);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid_g = (int64_t)sms * per_sm;
+    if (grid_g > ng) grid_g = ng > 0 ? ng : 1;
+    info.grid_g = (int)grid_g;
     return cudaSuccess;
 }
 
@@ -1344,13 +1361,23 @@ cudaError_t kmeans_batch_launch(const KmeansBatchInfo &info, unsigned char *dev_
     }
     if (info.ntasks == 0) return cudaSuccess;
     unsigned int *ticket = reinterpret_cast<unsigned int *>(dev_table + info.ticket_off);
-    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
+    const KmTask *tasks = reinterpret_cast<const KmTask *>(dev_table + info.tasks_off);
     // op 1: full sums (after a reset), op 2: incremental
-    kmeans_batch_kernel<<<(unsigned)info.grid, kThreads, info.smem, s>>>(
-        Ps, reinterpret_cast<const KmTask *>(dev_table + info.tasks_off), info.ntasks, ticket,
-        info.mu_cap, op == 1 ? 1 : 2);
-    return cudaGetLastError();
+    if (info.ntasks_smem > 0) {
+        kmeans_batch_kernel<<<(unsigned)info.grid, kThreads, info.smem, s>>>(
+            Ps, tasks, info.ntasks_smem, ticket, info.mu_cap, op == 1 ? 1 : 2);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (info.ntasks > info.ntasks_smem) {
+        kmeans_batch_kernel<<<(unsigned)info.grid_g, kThreads, info.smem_g, s>>>(
+            Ps, tasks + info.ntasks_smem, info.ntasks - info.ntasks_smem, ticket + 1, 0,
+            op == 1 ? 1 : 2);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_kmeans_finalize(const sk_ctx &c, int K, const double *S,

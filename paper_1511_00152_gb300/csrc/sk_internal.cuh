@@ -182,6 +182,11 @@ struct KmeansBatchInfo {
     size_t params_off, tasks_off, start_off, ticket_off, smem;
     int64_t total;
     int nd, ntasks, grid, mu_cap;
+    // tasks [ntasks_smem, ntasks) read their centre table from global memory
+    // and run as a second launch with the staging region alone (smem_g
+    // bytes, grid_g CTAs), leaving the rest of the SM's memory to L1
+    int ntasks_smem, grid_g;
+    size_t smem_g;
 };
 cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd,
                                std::vector<unsigned char> &table, KmeansBatchInfo &info);
