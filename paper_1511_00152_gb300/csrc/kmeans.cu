@@ -1255,7 +1255,7 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
     const size_t stage_region = (size_t)smem_max - mu_cap;
     std::vector<KmTask> tasks;
     int64_t total = 0;
-    size_t stage_used = 0;
+    size_t stage_used = 0, stage_used_g = 0;  // all data sets / global-table ones
     for (int d = 0; d < nd; ++d) {
         const sk_ctx &c = ctxs[d];
         KmParams &P = Ps[d];
@@ -1286,6 +1286,7 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
         const bool staged = st_b <= stage_region;
         P.stage_cap = staged ? P.RW * P.m : 0;
         if (staged && st_b > stage_used) stage_used = st_b;
+        if (staged && !mu_smem && P.mu_t && st_b > stage_used_g) stage_used_g = st_b;
         const int variant = (mu_smem ? 1 : (P.mu_t ? 4 : 0)) | (staged ? 2 : 0);
         const int64_t per = (int64_t)kWarpsK * P.RW * 16;  // 16 passes per warp
         for (int64_t r = 0; r < P.n; r += per) {
@@ -1335,8 +1336,9 @@ cudaError_t kmeans_batch_build(const sk_ctx *ctxs, const BatchKmeans *it, int nd
     const int na = info.ntasks_smem, ng = info.ntasks - info.ntasks_smem;
     if (grid > na) grid = na > 0 ? na : 1;
     info.grid = (int)grid;
-    // the global-table launch: staging only
-    info.smem_g = stage_used;
+    // the global-table launch: its data sets' staging only (the rest of the
+    // SM's memory goes to L1, which holds the tables' hot lines)
+    info.smem_g = stage_used_g;
     per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmeans_batch_kernel, kThreads,
                                                   info.smem_g);
