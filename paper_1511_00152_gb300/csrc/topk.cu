@@ -107,12 +107,74 @@ __device__ __forceinline__ float to_f32_rz(double x, int t) {
     return e <= 0 ? 0.f : __uint_as_float(bits);
 }
 
+// Double-float number h + l (two float32s, |l| below half an ulp of h or
+// so): the float64 panels' arithmetic on this GPU, whose float32 FMA rate is
+// about thirty times its float64 rate.  A product of two double-float
+// numbers is formed with the error-free float32 product (an FMA gives the
+// rounding error of h1 h2 exactly) plus the cross terms h1 l2 and l1 h2 (l1
+// l2 is dropped), and is added to the accumulator with Knuth's TwoSum;
+// about 2^-44 relative per product, twelve float32 operations.
+struct DF {
+    float h, l;
+};
+
+// The part of x that to_f32_rz(x, 0) dropped (the mantissa's low 29 bits,
+// rounded to float32), from the bit pattern on the integer units.
+__device__ __forceinline__ float f64_tail(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7FFu) - 1023 - 52;  // weight of the mantissa's bit 0
+    const uint32_t m29 = (uint32_t)(u & 0x1FFFFFFFull);
+    if (m29 == 0u || e < -126 || e > 127 - 29) return 0.f;
+    const float v = __uint2float_rn(m29) * __int_as_float((e + 127) << 23);
+    return (u >> 63) ? -v : v;
+}
+
 template <typename T>
 __device__ __forceinline__ T panel_in(double x, int t);
 template <>
 __device__ __forceinline__ double panel_in<double>(double x, int) { return x; }
 template <>
 __device__ __forceinline__ float panel_in<float>(double x, int t) { return to_f32_rz(x, t); }
+template <>
+__device__ __forceinline__ DF panel_in<DF>(double x, int) {
+    const float h = to_f32_rz(x, 0);
+    return DF{h, h == 0.f ? 0.f : f64_tail(x)};
+}
+
+template <typename T>
+__device__ __forceinline__ T panel_zero() {
+    return T(0);
+}
+template <>
+__device__ __forceinline__ DF panel_zero<DF>() {
+    return DF{0.f, 0.f};
+}
+
+// acc + a b
+template <typename T>
+__device__ __forceinline__ T panel_fma(T a, T b, T acc) {
+    return fma(a, b, acc);
+}
+template <>
+__device__ __forceinline__ DF panel_fma<DF>(DF a, DF b, DF acc) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const float t = __fadd_rn(acc.h, p);
+    const float z = __fsub_rn(t, acc.h);
+    const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(t, z)), __fsub_rn(p, z));
+    return DF{t, __fadd_rn(acc.l, __fadd_rn(err, e))};
+}
+
+template <typename T>
+__device__ __forceinline__ double panel_out(T x) {
+    return (double)x;
+}
+template <>
+__device__ __forceinline__ double panel_out<DF>(DF x) {
+    return (double)x.h + (double)x.l;
+}
 
 // *tshift = -(binary exponent of max_i |C_ii|): the float32 panels read C
 // scaled by 2^tshift, which puts the largest diagonal entry near 1 (the
@@ -176,7 +238,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const double *C, c
             const int c = e / kPanelJ, jj = e - c * kPanelJ;
             vr[r] = (e < kPanelJ * BC && c < b && j0 + jj < je)
                         ? panel_in<T>(V[(int64_t)c * pt + j0 + jj], 0)
-                        : T(0);
+                        : panel_zero<T>();
         }
     };
     auto store_v = [&](int q, const T (&vr)[VPT]) {
@@ -190,7 +252,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const double *C, c
 
     T acc[BC];
 #pragma unroll
-    for (int c = 0; c < BC; ++c) acc[c] = T(0);
+    for (int c = 0; c < BC; ++c) acc[c] = panel_zero<T>();
     if (nch > 0) {
         T vr[VPT];
         issue_c(0);
@@ -212,7 +274,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const double *C, c
         for (int jj = 0; jj < kPanelJ; ++jj) {
             const T cv = panel_in<T>(Cs[q & 1][jj][tid], tC);
 #pragma unroll
-            for (int c = 0; c < BC; ++c) acc[c] = fma(cv, Vs[q & 1][jj][c], acc[c]);
+            for (int c = 0; c < BC; ++c) acc[c] = panel_fma<T>(cv, Vs[q & 1][jj][c], acc[c]);
         }
         if (more) store_v(q + 1, vr);
         __syncthreads();
@@ -221,7 +283,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const double *C, c
     if (i < pt) {
 #pragma unroll
         for (int c = 0; c < BC; ++c)
-            if (c < b) atomicAdd(W + (int64_t)c * pt + i, (double)acc[c]);
+            if (c < b) atomicAdd(W + (int64_t)c * pt + i, panel_out<T>(acc[c]));
     }
 }
 
@@ -752,7 +814,7 @@ cudaError_t panel_launch(dim3 grid, const double *C, const double *V, int64_t pt
     if (f32)
         panel_kernel<BC, float><<<grid, kPanelThreads, 0, s>>>(C, V, pt, b, jlen, tshift, W);
     else
-        panel_kernel<BC, double><<<grid, kPanelThreads, 0, s>>>(C, V, pt, b, jlen, tshift, W);
+        panel_kernel<BC, DF><<<grid, kPanelThreads, 0, s>>>(C, V, pt, b, jlen, tshift, W);
     return cudaGetLastError();
 }
 
