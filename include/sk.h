@@ -168,11 +168,13 @@ sk_status sk_cov_finalize_centred(const sk_ctx *ctx, const double *G, const doub
 /* Top-k principal subspace of the symmetric pt x pt estimate C (device
  * float64), Sec. V PCA: eigenvalues (device float64, k, descending) and
  * eigenvectors (device float64, pt x k column-major, i.e. vector c at
- * U[c*pt .. c*pt+pt)) by block subspace iteration with Rayleigh-Ritz in
- * float64 on the device (the last two products with C, the Rayleigh-Ritz
- * product and the final basis and eigenproblem in float64; the earlier
- * products in float32 and the intermediate re-orthonormalisations, which do
- * not change the iterated subspace, from float32 factors).  iters is the
+ * U[c*pt .. c*pt+pt)) by block subspace iteration with Rayleigh-Ritz to
+ * float64 accuracy on the device (the last two products with C and the
+ * Rayleigh-Ritz product in double-float arithmetic, pairs of float32 with
+ * error-free products, about 2^-44 relative; the final basis and
+ * eigenproblem in float64; the earlier products in float32 and the
+ * intermediate re-orthonormalisations, which do not change the iterated
+ * subspace, from float32 factors).  iters is the
  * number of iterations (0 is taken as 1); the subspace error shrinks by about
  * (lambda_{b+1} / lambda_k)^iters with b = min(pt, 64, max(k + 8, 2k)).
  * work is a device float64 scratch buffer of sk_cov_topk_workspace(pt, k)

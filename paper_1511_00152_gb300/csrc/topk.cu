@@ -1,13 +1,14 @@
 // topk.cu -- top-k principal subspace of the symmetric pt x pt estimate C_n
-// (Sec. V: PCA recovers the leading eigenvectors of the covariance), in
-// float64 on the device.
+// (Sec. V: PCA recovers the leading eigenvectors of the covariance), to
+// float64 accuracy on the device.
 //
 // Block subspace iteration with b = min(pt, 64, max(k + 8, 2k)) columns:
 //   W = C V;  V = W R^{-1} with R the Cholesky factor of W^T W (CholQR),
 // repeated `iters` times (at least once) from a seeded start, the last
 // CholQR in float64 and the earlier ones from a float32 factor (see
 // chol32_kernel), the products C V of all but the last two iterations in
-// float32 (see panel_kernel), then one Rayleigh-Ritz step:
+// float32 and the last two in double-float (see panel_kernel and DF), then
+// one Rayleigh-Ritz step:
 // H = V^T C V (b x b), H = Q diag(lambda) Q^T, and U = V Q restricted to the
 // k largest lambda.  Each eigenvector's sign makes its largest-magnitude
 // entry positive.
@@ -74,10 +75,11 @@ __global__ void init_v_kernel(double *V, int64_t pt, int b, uint32_t k0, uint32_
 // use (two buffers), and V's slice of the chunk is staged in shared memory
 // and read as a broadcast.  W is zeroed before the launch and receives the
 // partial sums with double atomics.
-// T is the arithmetic: double, or float for the early iterations (C, scaled
-// by 2^tshift, and V rounded to float as they are read, float products and
-// sums; W then holds 2^tshift C V), whose only job is to turn V towards the
-// dominant subspace.
+// T is the arithmetic: DF (double-float, below) for the products that need
+// float64 accuracy, double (the float64 pipe), or float for the early
+// iterations (C, scaled by 2^tshift, and V rounded to float as they are
+// read, float products and sums; W then holds 2^tshift C V), whose only job
+// is to turn V towards the dominant subspace.
 constexpr int kPanelThreads = 128;
 constexpr int kPanelJ = 16;
 
@@ -108,8 +110,9 @@ __device__ __forceinline__ float to_f32_rz(double x, int t) {
 }
 
 // Double-float number h + l (two float32s, |l| below half an ulp of h or
-// so): the float64 panels' arithmetic on this GPU, whose float32 FMA rate is
-// about thirty times its float64 rate.  A product of two double-float
+// so): the arithmetic of the panels that need float64 accuracy on this GPU,
+// whose float32 FMA rate is about thirty times its float64 rate.  A
+// product of two double-float
 // numbers is formed with the error-free float32 product (an FMA gives the
 // rounding error of h1 h2 exactly) plus the cross terms h1 l2 and l1 h2 (l1
 // l2 is dropped), and is added to the accumulator with Knuth's TwoSum;
@@ -868,9 +871,10 @@ cudaError_t launch_topk(const sk_ctx &c, const double *C, int k, int iters, doub
     int ublocks = (int)((k * pt + 255) / 256);
     if (ublocks > 4 * sms) ublocks = 4 * sms;
     // at least one CholQR, the last one in float64; the last three panel
-    // products (two power steps and the Rayleigh-Ritz product) in float64,
-    // the earlier ones in float32: each float64 step shrinks the float32
-    // rounding left in span(V) by the gap ratio lambda_{b+1} / lambda_k.
+    // products (two power steps and the Rayleigh-Ritz product) in
+    // double-float, the earlier ones in float32: each double-float step
+    // shrinks the float32 rounding left in span(V) by the gap ratio
+    // lambda_{b+1} / lambda_k.
     const int n_it = iters > 0 ? iters : 1;
     const unsigned g32blocks = (unsigned)((pt + kG32Rows - 1) / kG32Rows);
     init_v_kernel<<<eblocks, 256, 0, s>>>(w.V, pt, b, k0, k1);
