@@ -76,8 +76,7 @@ __global__ void init_v_kernel(double *V, int64_t pt, int b, uint32_t k0, uint32_
 // and read as a broadcast.  W is zeroed before the launch and receives the
 // partial sums with double atomics.
 // T is the arithmetic: DF (double-float, below) for the products that need
-// float64 accuracy, double (the float64 pipe), or float for the early
-// iterations (C, scaled by 2^tshift, and V rounded to float as they are
+// float64 accuracy, or float for the early iterations (C, scaled by 2^tshift, and V rounded to float as they are
 // read, float products and sums; W then holds 2^tshift C V), whose only job
 // is to turn V towards the dominant subspace.
 constexpr int kPanelThreads = 128;
@@ -134,8 +133,6 @@ __device__ __forceinline__ float f64_tail(double x) {
 
 template <typename T>
 __device__ __forceinline__ T panel_in(double x, int t);
-template <>
-__device__ __forceinline__ double panel_in<double>(double x, int) { return x; }
 template <>
 __device__ __forceinline__ float panel_in<float>(double x, int t) { return to_f32_rz(x, t); }
 template <>
