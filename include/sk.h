@@ -370,7 +370,8 @@ sk_status sk_mean_accumulate(const sk_ctx *ctx, const int32_t *idx, const float 
 sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_total,
                            double *mean, void *stream);
 
-/* ---- Many data sets, one launch per stage (no paper counterpart: the
+/* ---- Many data sets, one launch per stage (two for a K-means pass; no
+ * paper counterpart: the
  * paper's method applied to a batch of independent data sets).
  *
  * Each item describes one data set with its own p, m, seed and K and the
@@ -446,9 +447,12 @@ sk_status sk_batch_cov_accumulate(const sk_batch *b, void *stream);
 /* Zeroes every data set's S, cnt, nk in one launch. */
 sk_status sk_batch_kmeans_reset(const sk_batch *b, void *stream);
 
-/* One K-means pass over every data set in one persistent launch:
- * incremental = 0 as sk_kmeans_step (after sk_batch_kmeans_reset),
- * incremental = 1 as sk_kmeans_step_delta. */
+/* One K-means pass over every data set: incremental = 0 as sk_kmeans_step
+ * (after sk_batch_kmeans_reset), incremental = 1 as sk_kmeans_step_delta.
+ * Two persistent launches: the data sets whose centre table fits shared
+ * memory (or that keep none), then those reading it from global memory,
+ * which run with the staging region alone so that L1 can hold their
+ * tables' lines. */
 sk_status sk_batch_kmeans_step(const sk_batch *b, int32_t incremental, void *stream);
 
 /* sk_kmeans_finalize of every data set in one launch. */
