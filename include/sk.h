@@ -371,8 +371,8 @@ sk_status sk_mean_finalize(const sk_ctx *ctx, const double *sums, int64_t n_tota
                            double *mean, void *stream);
 
 /* ---- Many data sets, one launch per stage (two for a K-means pass; no
- * paper counterpart: the
- * paper's method applied to a batch of independent data sets).
+ * paper counterpart: the paper's method applied to a batch of independent
+ * data sets).
  *
  * Each item describes one data set with its own p, m, seed and K and the
  * device buffers of every stage: raw rows X (n x p, leading dimension ldx,
