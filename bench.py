@@ -512,7 +512,9 @@ def run_gpu(args, cfg):
         # X streams to the device in chunks; each chunk is compressed and added
         # to the Gram while the next ones are copied (a ring of three chunk
         # buffers on the device)
-        streamer = pipeline.HostStreamer(ctx, (n + 7) // 8, mode, nbuf=3, device=dev)
+        nchunk = max(1, args.e2e_chunks)
+        streamer = pipeline.HostStreamer(ctx, (n + nchunk - 1) // nchunk, mode, nbuf=3,
+                                         device=dev)
 
         def e2e_step():
             Xsel2.copy_(Xsel_h, non_blocking=True)
@@ -1073,6 +1075,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=200_000)
     ap.add_argument("--ref-rows", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="chunks of X per end-to-end step (host-to-device copy ring)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip timing the plain FP32 Gram beside the chosen mode")
