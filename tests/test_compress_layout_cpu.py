@@ -11,8 +11,13 @@ warps.  In shared memory element e sits at phys(e) = e + 4 floor(e / 128)
 that every phase covers each element once, that the butterflies of all
 phases together run over every element bit of a row exactly once (so the
 composition is the Walsh-Hadamard transform, whose stages commute), and
-that every warp-wide shared-memory access is free of bank conflicts.
+that every warp-wide shared-memory access is free of bank conflicts.  Two
+more host checks: the split gather (pt > 1024, masks drawn first) covers
+each sample once with its early-fetched coordinates, and the masks-alone
+kernel's 16-bit virtual Fisher-Yates entries (value and row tag) behave as
+a fresh array per row across tag wraps.
 """
+import numpy as np
 import pytest
 
 SEG = 1024 + 32
@@ -138,3 +143,53 @@ def test_unit_addresses_match_the_gather():
     for c in range(0, 1 << L, 13):
         addr = (c >> 10) * SEG + phys(c & 1023)
         assert addr // SEG == c >> 10 and addr % SEG == phys(c & 1023)
+
+
+@pytest.mark.parametrize("L", [11, 12, 13])
+@pytest.mark.parametrize("m", [1, 41, 64, 205, 819, 1640])
+def test_split_gather_covers_each_sample_once(L, m):
+    """pt > 1024 with the masks drawn first: the G warps of a row group
+    gather its m samples, each lane first the kMI = 2 coordinates it fetched
+    before the transform (t = 32 wg + lane + q 32 G), then the rest in steps
+    of 32 G; every t in [0, m) exactly once."""
+    G, kMI = 1 << (L - 10), 2
+    seen = []
+    for wg in range(G):
+        for lane in range(32):
+            for q in range(kMI):
+                t = wg * 32 + lane + q * G * 32
+                if t < m:
+                    seen.append(t)
+            t = wg * 32 + lane + kMI * G * 32
+            while t < m:
+                seen.append(t)
+                t += G * 32
+    assert sorted(seen) == list(range(m))
+
+
+@pytest.mark.parametrize("L", [6, 10, 12, 13])
+def test_sixteen_bit_fisher_yates_entries(L):
+    """The masks-alone kernel's virtual Fisher-Yates array with 16-bit
+    entries: an L-bit value under a (16 - L)-bit row tag; a row sees only its
+    own writes (other positions read as their own index), and clearing the
+    array when the tag wraps keeps an old row's entries from ever matching.
+    Checked against a fresh dictionary per row over several wraps."""
+    PT, tag_max = 1 << L, (1 << (16 - L)) - 1
+    A = np.zeros(PT, dtype=np.uint16)
+    rng = np.random.default_rng(L)
+    tag = 1
+    for row in range(3 * tag_max + 5):
+        ref = {}
+        for _ in range(40):
+            k = int(rng.integers(0, PT))
+            if rng.random() < 0.5:
+                v = int(rng.integers(0, PT))
+                A[k] = (tag << L) | v
+                ref[k] = v
+            a = int(A[k])
+            got = a & (PT - 1) if (a >> L) == tag else k
+            assert got == ref.get(k, k)
+        tag += 1
+        if tag > tag_max:
+            A[:] = 0
+            tag = 1
